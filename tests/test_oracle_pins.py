@@ -1,0 +1,430 @@
+"""Pins of the FP64 oracle against facts fixed outside it (CPU only).
+
+Each test checks the oracle against something other than itself: hand-typed
+closed forms (tests/golden), independent library routines (numpy.fft for the
+*dense* definitions, scipy.linalg constructors, numpy.kron), mathematical
+invariants (adjoint identity, unitarity, diagonalisation, H H^T = n I, the
+mixed-product rule) and brute force on tiny inputs.  ``test_planted_*`` plant
+a plausible mistake in a copy of the oracle and check that a pin catches it.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import oracle as O
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+RNG = np.random.default_rng(1234)
+
+
+def crand(*shape):
+    return RNG.standard_normal(shape) + 1j * RNG.standard_normal(shape)
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300)
+
+
+def _golden(name):
+    rows = []
+    for line in open(os.path.join(GOLD, name)):
+        if line.strip() and not line.startswith("#"):
+            rows.append(line.split())
+    return rows
+
+
+def _kv(name):
+    return {r[0]: np.array([float(v) for v in r[1:]]) for r in _golden(name)}
+
+
+# ----------------------------------------------------------------- golden, hand-typed
+def test_golden_dft4():
+    want = np.array([[complex(*map(float, e.split(","))) for e in r] for r in _golden("dft4.txt")])
+    assert np.allclose(O.Fourier(4).dense(), want, atol=1e-15)
+
+
+def test_golden_hadamard8():
+    want = np.array([[int(v) for v in r] for r in _golden("hadamard8.txt")])
+    assert np.array_equal(O.Hadamard(8).dense(), want)
+
+
+def test_golden_circulant3():
+    g = _kv("circulant3.txt")
+    C = O.Circulant(g["c"])
+    assert np.allclose(C.dense() @ g["x"], g["y"])
+    assert np.allclose(C.apply(g["x"]), g["y"])
+    assert np.allclose(C.apply(g["x"], adjoint=True), g["yadj"])
+
+
+def test_golden_toeplitz3():
+    g = _kv("toeplitz3.txt")
+    T = O.Toeplitz(g["t"], 3, 3)
+    assert np.allclose(T.dense() @ g["x"], g["y"])
+    assert np.allclose(T.apply(g["x"]), g["y"])
+    assert np.allclose(T.apply(g["x"], adjoint=True), g["yadj"])
+
+
+# ----------------------------------------------------------------- Fourier, Eq. (1)
+@pytest.mark.parametrize("n", [1, 2, 3, 8, 12, 64, 256])
+def test_fourier_dense_matches_library_dft(n):
+    # numpy's FFT of the identity columns is an independent evaluation of Eq. (1)
+    assert rel(O.Fourier(n).dense(), np.fft.fft(np.eye(n), axis=0)) < 1e-13
+
+
+@pytest.mark.parametrize("n", [8, 64, 1024])
+def test_fourier_closed_forms(n):
+    F = O.Fourier(n)
+    e0 = np.zeros(n)
+    e0[0] = 1
+    assert np.allclose(F.apply(e0), np.ones(n))               # DFT of an impulse
+    m = 3 % n
+    j = np.arange(n)
+    tone = np.exp(2j * np.pi * m * j / n)                      # DFT of a tone is n * e_m
+    want = np.zeros(n, complex)
+    want[m] = n
+    assert np.allclose(F.apply(tone), want, atol=1e-9)
+    x = crand(n)
+    assert np.isclose(np.linalg.norm(F.apply(x)) ** 2, n * np.linalg.norm(x) ** 2)  # Parseval
+    D = F.dense()
+    assert rel(D.conj().T @ D, n * np.eye(n)) < 1e-12          # F^H F = n I
+    U = O.Fourier(n, ortho=True).dense()
+    assert rel(U.conj().T @ U, np.eye(n)) < 1e-12              # F / sqrt(n) is unitary
+
+
+@pytest.mark.parametrize("n,ortho", [(16, False), (12, True), (512, False)])
+def test_fourier_fast_route_matches_definition(n, ortho):
+    F = O.Fourier(n, ortho)
+    X = crand(n, 3)
+    D = F.dense()
+    assert rel(F.apply(X), D @ X) < 1e-12
+    assert rel(F.apply(X, adjoint=True), D.conj().T @ X) < 1e-12
+    for i in [0, 1, n - 1]:
+        assert rel(F.row(i), D[i]) < 1e-13
+
+
+# ----------------------------------------------------------------- Circulant, Eq. (5)
+@pytest.mark.parametrize("n", [1, 5, 16, 128])
+def test_circulant_dense_matches_scipy(n):
+    c = crand(n)
+    assert np.array_equal(O.Circulant(c).dense(), sla.circulant(c))
+
+
+@pytest.mark.parametrize("n", [8, 64, 100])
+def test_circulant_diagonalised_by_dft(n):
+    c = crand(n)
+    C = O.Circulant(c).dense()
+    F = O.Fourier(n).dense()
+    # F C F^H = n Diag(F c)
+    assert rel(F @ C @ F.conj().T, n * np.diag(F @ c)) < 1e-11
+    # commutes with the cyclic shift
+    S = np.roll(np.eye(n), 1, axis=0)
+    assert rel(S @ C, C @ S) < 1e-14
+
+
+@pytest.mark.parametrize("n", [8, 64, 100, 4096])
+def test_circulant_fast_route_matches_definition(n):
+    C = O.Circulant(crand(n))
+    X = crand(n, 2)
+    D = C.dense()
+    assert rel(C.apply(X), D @ X) < 1e-12
+    assert rel(C.apply(X, adjoint=True), D.conj().T @ X) < 1e-12
+    Cr = O.Circulant(RNG.standard_normal(n))
+    xr = RNG.standard_normal((n, 2))
+    yr = Cr.apply(xr)
+    assert yr.dtype == np.float64 and rel(yr, Cr.dense() @ xr) < 1e-12
+
+
+# ----------------------------------------------------------------- Toeplitz (Sec. 2.1.1)
+@pytest.mark.parametrize("rows,cols", [(1, 1), (3, 3), (7, 7), (5, 9), (9, 5), (64, 64), (100, 37)])
+def test_toeplitz_dense_matches_scipy(rows, cols):
+    t = crand(rows + cols - 1)
+    col, row = t[:rows], np.concatenate([t[:1], t[rows:]])
+    assert np.array_equal(O.Toeplitz(t, rows, cols).dense(), sla.toeplitz(col, row))
+
+
+@pytest.mark.parametrize("rows,cols", [(3, 3), (64, 64), (5, 9), (9, 5), (1024, 1024), (100, 37)])
+def test_toeplitz_embedding_matches_definition(rows, cols):
+    T = O.Toeplitz(crand(rows + cols - 1), rows, cols)
+    assert T.L >= rows + cols - 1 and (T.L & (T.L - 1)) == 0
+    D = T.dense()
+    X = crand(cols, 2)
+    Y = crand(rows, 2)
+    assert rel(T.apply(X), D @ X) < 1e-12
+    assert rel(T.apply(Y, adjoint=True), D.conj().T @ Y) < 1e-12
+    # embedding identity: T = [I 0] C_L [I; 0]
+    C = O.Circulant(T.embed).dense()
+    assert rel(C[:rows, :cols], D) < 1e-15
+
+
+def test_toeplitz_embedding_any_length():
+    # the identity holds for any embedding length >= rows + cols - 1, not only 2^k
+    rows, cols = 6, 4
+    t = crand(rows + cols - 1)
+    D = O.Toeplitz(t, rows, cols).dense()
+    for L in [9, 10, 13]:
+        c = np.zeros(L, complex)
+        c[:rows] = t[:rows]
+        c[L - (cols - 1):] = t[rows:][::-1]
+        assert rel(O.Circulant(c).dense()[:rows, :cols], D) < 1e-15
+
+
+# ----------------------------------------------------------------- Hadamard (textbook)
+@pytest.mark.parametrize("n", [1, 2, 4, 16, 256])
+def test_hadamard_dense_matches_scipy(n):
+    assert np.array_equal(O.Hadamard(n).dense(), sla.hadamard(n))
+
+
+@pytest.mark.parametrize("n", [2, 64, 1024])
+def test_hadamard_invariants(n):
+    H = O.Hadamard(n)
+    D = H.dense()
+    assert np.array_equal(D @ D.T, n * np.eye(n, dtype=np.int64))    # H H^T = n I
+    x = RNG.integers(-128, 128, size=(n, 3))
+    assert np.array_equal(H.apply(H.apply(x)), n * x)                # H H x = n x, exact int64
+    e0 = np.zeros((n, 1), dtype=np.int64)
+    e0[0] = 1
+    assert np.array_equal(H.apply(e0)[:, 0], np.ones(n, dtype=np.int64))
+    assert np.array_equal(H.apply(x), D @ x)                         # butterflies = definition
+    xf = crand(n, 2)
+    assert rel(H.apply(xf), D @ xf) < 1e-13
+
+
+def test_hadamard_int8_extremes_exact():
+    n = 1 << 16
+    x = np.full((n, 1), -128, dtype=np.int8)
+    y = O.Hadamard(n).apply(x)
+    assert y.dtype == np.int64 and y[0, 0] == -128 * n and np.all(y[1:, 0] == 0)
+    assert abs(int(y[0, 0])) <= 2 ** 23
+
+
+# ----------------------------------------------------------------- Diag, Partial
+def test_diag_and_partial():
+    n = 50
+    d = crand(n)
+    Dg = O.Diag(d)
+    x = crand(n, 2)
+    assert np.allclose(Dg.apply(x), np.diag(d) @ x)
+    assert np.allclose(Dg.apply(x, adjoint=True), np.diag(d.conj()) @ x)
+    idx = np.sort(RNG.choice(n, 17, replace=False))
+    P = O.Partial(idx, n)
+    ramp = np.arange(n, dtype=np.float64)
+    assert np.array_equal(P.apply(ramp), idx.astype(np.float64))     # forward on x_j = j gives idx
+    for r in [0, 5, 16]:
+        e = np.zeros(17)
+        e[r] = 1
+        z = P.apply(e, adjoint=True)
+        assert z[idx[r]] == 1 and np.count_nonzero(z) == 1           # adjoint of e_r is e_idx[r]
+    with pytest.raises(ValueError):
+        O.Partial([n], n)
+
+
+# ----------------------------------------------------------------- composites
+def _zoo(n=16):
+    c = crand(n)
+    d = np.exp(2j * np.pi * RNG.random(n))
+    idx = np.sort(RNG.choice(n, n // 4, replace=False))
+    t = crand(2 * n - 1)
+    return {
+        "fourier": O.Fourier(n),
+        "fourier_ortho": O.Fourier(n, True),
+        "circulant": O.Circulant(c),
+        "toeplitz": O.Toeplitz(t, n, n),
+        "toeplitz_rect": O.Toeplitz(crand(n + 5 - 1), n, 5),
+        "hadamard": O.Hadamard(n),
+        "diag": O.Diag(d),
+        "partial": O.Partial(idx, n),
+        "product_PDC": O.Product(O.Partial(idx, n), O.Diag(d), O.Circulant(c)),
+        "sum": O.Sum(O.Circulant(c), O.Hadamard(n), O.Fourier(n)),
+        "blkdiag": O.BlkDiag(O.Fourier(4), O.Partial([1, 3], 5), O.Hadamard(8)),
+        "kron": O.Kron(O.Hadamard(4), O.Circulant(crand(4)), O.Fourier(2)),
+        "kron_rect": O.Kron(O.Partial([0, 2], 3), O.Fourier(4)),
+        "nested": O.Product(O.Kron(O.Fourier(4), O.Fourier(4)), O.Diag(d),
+                            O.Kron(O.Fourier(4), O.Fourier(4))),
+    }
+
+
+@pytest.mark.parametrize("name", list(_zoo().keys()))
+def test_adjoint_identity(name):
+    A = _zoo()[name]
+    x = crand(A.cols)
+    y = crand(A.rows)
+    lhs = np.vdot(y, A.apply(x))                 # <A x, y>
+    rhs = np.vdot(A.apply(y, adjoint=True), x)   # <x, A^H y>
+    assert abs(lhs - rhs) <= 1e-10 * max(1.0, abs(lhs))
+
+
+@pytest.mark.parametrize("name", list(_zoo().keys()))
+def test_rows_and_apply_match_dense(name):
+    A = _zoo()[name]
+    D = A.dense()
+    X = crand(A.cols, 2)
+    assert rel(A.apply(X), D @ X) < 1e-12
+    Y = crand(A.rows, 2)
+    assert rel(A.apply(Y, adjoint=True), D.conj().T @ Y) < 1e-12
+    for i in sorted({0, A.rows // 2, A.rows - 1}):
+        assert rel(A.row(i), D[i]) < 1e-12
+
+
+def test_product_order():
+    A, B = O.Diag(crand(6)), O.Fourier(6)
+    P = O.Product(A, B)
+    assert rel(P.dense(), A.dense() @ B.dense()) < 1e-14
+    assert rel(P.dense(), B.dense() @ A.dense()) > 1e-3       # order matters
+
+
+def test_kron_definition_matches_numpy_kron():
+    fs = [O.Hadamard(4), O.Circulant(crand(4)), O.Fourier(4)]
+    K = O.Kron(*fs)
+    want = np.kron(fs[0].dense(), np.kron(fs[1].dense(), fs[2].dense()))
+    assert rel(K.dense(), want) < 1e-14
+
+
+def test_kron_mixed_product():
+    A, B = O.Circulant(crand(4)), O.Fourier(8)
+    C, D = O.Diag(crand(4)), O.Hadamard(8)
+    lhs = O.Kron(A, B).dense() @ O.Kron(C, D).dense()
+    rhs = O.Kron(O.Product(A, C), O.Product(B, D)).dense()
+    assert rel(lhs, rhs) < 1e-13
+
+
+def test_kron_analogue_4096_by_adjoint_and_rows():
+    # the 2^12 analogue of Kron(H_256, C_1024, F_64) keeps the three-factor structure
+    K = O.Kron(O.Hadamard(16), O.Circulant(crand(16)), O.Fourier(16))
+    x = crand(K.cols)
+    y = K.apply(x)
+    for i in [0, 17, 4095]:
+        assert abs(np.dot(K.row(i), x) - y[i]) < 1e-9 * np.linalg.norm(y)
+    z = crand(K.rows)
+    assert abs(np.vdot(z, y) - np.vdot(K.apply(z, adjoint=True), x)) < 1e-9 * abs(np.vdot(z, y))
+
+
+# ----------------------------------------------------------------- FISTA
+def test_soft_threshold_closed_forms():
+    z = np.array([-3.0, -1.0, -0.5, 0.0, 0.5, 1.0, 3.0])
+    assert np.array_equal(O.soft(z, 1.0), np.array([-2.0, 0.0, 0.0, 0.0, 0.0, 0.0, 2.0]))
+    zc = np.array([3 + 4j, 0.3 + 0.4j, 0j])
+    out = O.soft(zc, 1.0)
+    assert np.allclose(out, [(3 + 4j) * 0.8, 0, 0])
+
+
+def test_fista_orthonormal_closed_form():
+    # A = H / sqrt(n) is orthonormal: with L = 1 the lasso solution soft(A^T b, lambda) is
+    # reached at k = 1 and kept.
+    n = 64
+    A = O.Product(O.Diag(np.full(n, 1 / np.sqrt(n))), O.Hadamard(n))
+    b = RNG.standard_normal(n)
+    lam = 0.3
+    x_star = O.soft(A.apply(b, adjoint=True), lam)
+    for k in [1, 2, 7]:
+        assert np.allclose(O.fista(A, b, lam, 1.0, iters=k), x_star, atol=1e-12)
+
+
+def _small_problem(n=64, seed=7):
+    rng = np.random.default_rng(seed)
+    t = rng.standard_normal(2 * n - 1) / np.sqrt(n)
+    idx = np.sort(rng.choice(n, n // 2, replace=False))
+    A = O.Product(O.Partial(idx, n), O.Toeplitz(t, n, n))
+    x0 = np.zeros(n)
+    x0[rng.choice(n, 3, replace=False)] = rng.standard_normal(3)
+    b = A.apply(x0) + 0.01 * rng.standard_normal(n // 2)
+    return A, b
+
+
+def test_lipschitz_bounds_against_svd():
+    for seed in range(3):
+        A, _ = _small_problem(seed=seed)
+        smax2 = np.linalg.svd(A.dense(), compute_uv=False)[0] ** 2
+        T = A.terms[1]
+        cap = np.max(np.abs(T.spectrum)) ** 2
+        L = O.lipschitz(A, spectrum_cap=cap)
+        assert cap >= smax2 * (1 - 1e-12)            # the spectral cap is an upper bound
+        assert L >= smax2 * (1 - 1e-9) or L == cap   # safe step
+        assert L <= 1.05 * smax2 * (1 + 1e-9)
+
+
+def test_fista_rate_bound_and_kkt():
+    A, b = _small_problem()
+    lam = O.lambda_from_b(A, b)
+    smax2 = np.linalg.svd(A.dense(), compute_uv=False)[0] ** 2
+    L = 1.01 * smax2
+    x_star = O.fista(A, b, lam, L, iters=10000)
+    # KKT: |A^T (A x* - b)|_j <= lambda, with equality and the sign of -x_j on the support
+    g = A.apply(A.apply(x_star) - b, adjoint=True)
+    assert np.all(np.abs(g) <= lam * (1 + 1e-6))
+    on = np.abs(x_star) > 1e-9
+    assert np.any(on)
+    assert np.allclose(g[on], -lam * np.sign(x_star[on]), rtol=1e-5, atol=1e-9)
+    # Beck-Teboulle: F(x_k) - F* <= 2 L ||x_0 - x*||^2 / (k + 1)^2
+    F_star = O.objective(A, b, x_star, lam)
+    for k in [1, 5, 20, 100]:
+        xk = O.fista(A, b, lam, L, iters=k)
+        bound = 2 * L * np.linalg.norm(x_star) ** 2 / (k + 1) ** 2
+        assert O.objective(A, b, xk, lam) - F_star <= bound * (1 + 1e-9) + 1e-12
+
+
+def test_ista_monotone_and_resume():
+    A, b = _small_problem(seed=3)
+    lam = O.lambda_from_b(A, b)
+    L = 1.01 * np.linalg.svd(A.dense(), compute_uv=False)[0] ** 2
+    prev = np.inf
+    for k in range(1, 30):
+        f = O.objective(A, b, O.fista(A, b, lam, L, iters=k, accel=False), lam)
+        assert f <= prev + 1e-12                       # ISTA with step 1/L never increases F
+        prev = f
+    x1, st = O.fista(A, b, lam, L, iters=13, return_state=True)
+    x2 = O.fista(A, b, lam, L, iters=17, state=st)
+    assert np.array_equal(x2, O.fista(A, b, lam, L, iters=30))
+
+
+# ----------------------------------------------------------------- planted mistakes
+class _CirculantNoConj(O.Circulant):
+    def _apply(self, X, adjoint):                       # forgets the conjugate in the adjoint
+        return np.fft.ifft(self.spectrum[:, None] * np.fft.fft(X.astype(complex), axis=0), axis=0)
+
+
+class _ToeplitzOffByOne(O.Toeplitz):
+    def dense(self):                                    # upper triangle shifted by one
+        i = np.arange(self.rows)[:, None]
+        j = np.arange(self.cols)[None, :]
+        d = i - j
+        return np.where(d >= 0, self.t[np.clip(d, 0, None)],
+                        self.t[np.clip(self.rows - d, 0, len(self.t) - 1)])
+
+
+class _KronSwapped(O.Kron):
+    def dense(self):                                    # factors in the wrong order
+        return O.Kron(*self.factors[::-1]).dense()
+
+
+def test_planted_mistakes_are_caught():
+    n = 16
+    with pytest.raises(AssertionError):
+        A = _CirculantNoConj(crand(n))
+        x, y = crand(n), crand(n)
+        assert abs(np.vdot(y, A.apply(x)) - np.vdot(A.apply(y, adjoint=True), x)) < 1e-9
+    with pytest.raises(AssertionError):
+        t = crand(2 * n - 1)
+        col, row = t[:n], np.concatenate([t[:1], t[n:]])
+        assert np.array_equal(_ToeplitzOffByOne(t, n, n).dense(), sla.toeplitz(col, row))
+    with pytest.raises(AssertionError):
+        fs = [O.Hadamard(4), O.Fourier(4)]
+        assert rel(_KronSwapped(*fs).dense(), np.kron(fs[0].dense(), fs[1].dense())) < 1e-14
+
+
+# ----------------------------------------------------------------- input generators
+def test_inputs_deterministic_and_snr():
+    import fm_inputs as I
+    a = I.fista_instance(5)
+    b = I.fista_instance(5)
+    assert a["n"] == b["n"] and np.array_equal(a["t"], b["t"]) and np.array_equal(a["idx"], b["idx"])
+    inst = I.fista_instance(0, log2n_range=(10, 10))
+    n = inst["n"]
+    bb = I.fista_measurements(inst)
+    A = O.Product(O.Partial(inst["idx"], n), O.Toeplitz(inst["t"].astype(np.float64), n, n))
+    clean = A.apply(inst["x0"])
+    snr = 20 * np.log10(np.linalg.norm(clean) / np.linalg.norm(bb.astype(np.float64) - clean))
+    assert abs(snr - 30.0) < 0.01
+    c, X, Y = I.circulant_tiny(n=64, k=3)
+    assert X.shape == (3, 64) and X.dtype == np.complex128
