@@ -1,0 +1,211 @@
+/*
+ * fm.h -- C ABI of the GB300 structured-operator library (libfastmat_gb300.so).
+ *
+ * The library applies composed structured linear operators to blocks of
+ * columns on one GPU: the forward transform phi_A(X) = A X (Eq. (3) of the
+ * fastmat paper, arXiv 1710.09578) and the backward transform
+ * beta_A(Y) = A^H Y (Eq. (4)), plus a batched FISTA solver for the
+ * l1-regularised least-squares problem of Eq. (8) built on those two calls.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Column blocks.  A block of K columns of length n is stored column by column:
+ *   column k starts at element k*ld of the buffer, its n elements are
+ *   contiguous, ld >= n.  (A C-contiguous torch tensor of shape [K, n] is such a
+ *   block with ld = n.)  Element types are given by fm_dtype; complex types are
+ *   interleaved (re, im).
+ * Pointers.  Constructor parameter arrays may be host or device pointers (they
+ *   are copied with cudaMemcpyDefault and may be freed or changed afterwards:
+ *   operators are immutable, Sec. 2.1.1 of the paper).  Data buffers passed to
+ *   fm_forward / fm_backward / fm_fista are DEVICE pointers owned by the
+ *   caller.
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  All device work is enqueued on it; no call synchronises the
+ *   device unless stated.
+ * Errors.  Every call returns fm_status.  Argument checks run before any
+ *   launch and leave outputs untouched.  Asynchronous CUDA failures surface as
+ *   FM_ERR_CUDA from a later call.  fm_last_error() gives a one-line message
+ *   for the calling thread.  Nothing throws across this ABI.
+ * Ownership.  Constructors return a handle with one reference.  Composites
+ *   hold a reference to each child, so children may be released right after
+ *   the composite is built.  fm_release drops one reference.
+ */
+#ifndef FM_H
+#define FM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fm_op_s* fm_op;
+typedef struct fm_batch_s* fm_batch;
+
+typedef enum {
+  FM_OK = 0,
+  FM_ERR_INVALID_ARG = 1, /* null pointer, bad count or flag                        */
+  FM_ERR_SHAPE = 2,       /* sizes of composed operators or buffers disagree         */
+  FM_ERR_DTYPE = 3,       /* element type not accepted by the operator               */
+  FM_ERR_UNSUPPORTED = 4, /* valid request outside what this build implements        */
+  FM_ERR_ALIAS = 5,       /* output overlaps input where in-place is not allowed      */
+  FM_ERR_OOM = 6,         /* device allocation failed                                */
+  FM_ERR_CUDA = 7,        /* CUDA runtime error (launch or earlier asynchronous one) */
+  FM_ERR_TIMEOUT = 8,     /* a bounded device wait ran out                           */
+  FM_ERR_NUMERIC = 9      /* non-finite value met where a finite one is required     */
+} fm_status;
+
+typedef enum { FM_I8 = 0, FM_I32 = 1, FM_F32 = 2, FM_F64 = 3, FM_C64 = 4, FM_C128 = 5 } fm_dtype;
+
+/* Arithmetic of the Hadamard transform (the Sylvester matrix is exact +-1):
+ *   FM_HAD_FP32   f32 or c64 data, FP32 adds;
+ *   FM_HAD_BF16   f32 data rounded to BF16 and multiplied by 16x16 +-1 tiles on
+ *                 the tensor cores with FP32 accumulation (relative error ~1e-3);
+ *   FM_HAD_BF16X2 as BF16 but each stage splits x = hi + lo into two BF16
+ *                 parts and accumulates both products (FP32-level accuracy);
+ *   FM_HAD_INT8   int8 data, int32 output, exact. */
+typedef enum { FM_HAD_FP32 = 0, FM_HAD_BF16 = 1, FM_HAD_BF16X2 = 2, FM_HAD_INT8 = 3 } fm_had_mode;
+
+/* ---------------------------------------------------------------- constructors */
+
+/* Fourier matrix of Eq. (1), read 0-based: F[k, j] = exp(-2 pi i j k / n); F^H has
+ * the opposite sign and no 1/n.  ortho = 1 scales both by 1/sqrt(n).
+ * n must be a power of two, 1 <= n <= 2^24 (FM_ERR_UNSUPPORTED otherwise). */
+fm_status fm_fourier(int64_t n, int ortho, fm_op* out);
+
+/* Circulant matrix C[i, j] = c[(i - j) mod n] with first column c (Eq. (5):
+ * C x = ifft(fft(c) * fft(x)); Sec. 2.1.1: C = F^H Diag(F c / n) F with the
+ * spectrum computed once, in FP64, at construction).  dt in {F32, F64, C64, C128}.
+ * n a power of two, 1 <= n <= 2^24. */
+fm_status fm_circulant(const void* c, int64_t n, fm_dtype dt, void* stream, fm_op* out);
+
+/* Toeplitz matrix (Sec. 2.1.1: non-circular convolution in the frequency domain),
+ * rows x cols, T[i, j] = t[i - j] for i >= j and t[rows - 1 + j - i] for i < j, i.e.
+ * t = [first column (rows entries); first row without t0 (cols - 1 entries)].
+ * Applied through a circulant embedding of length L = 2^ceil(log2(rows + cols - 1)),
+ * L <= 2^24.  dt in {F32, F64, C64, C128}. */
+fm_status fm_toeplitz(const void* t, int64_t rows, int64_t cols, fm_dtype dt, void* stream,
+                      fm_op* out);
+
+/* Sylvester Hadamard matrix H[i, j] = (-1)^popcount(i & j), natural order,
+ * unnormalised, n = 2^log2n, 0 <= log2n <= 24 (BF16 modes: 4 <= log2n <= 16).
+ * Symmetric, so forward and backward are the same map. */
+fm_status fm_hadamard(int log2n, fm_had_mode mode, fm_op* out);
+
+/* Diagonal matrix Diag(d) (Eq. (7)): y_i = d_i x_i, adjoint conj(d_i) y_i.
+ * dt in {F32, F64, C64, C128}. */
+fm_status fm_diag(const void* d, int64_t n, fm_dtype dt, void* stream, fm_op* out);
+
+/* Row selection P (the operator P of Eq. (7); "random selection of rows" in the
+ * compressed model of Sec. 3): m x n, y_r = x_{idx[r]}; the adjoint zero-fills and
+ * scatters.  idx (int32, host or device) must hold m distinct values in [0, n);
+ * FM_ERR_INVALID_ARG otherwise (checked on the host at construction). */
+fm_status fm_partial(const int32_t* idx, int64_t m, int64_t n, void* stream, fm_op* out);
+
+/* Compositions (Sec. 2.1.1: the transforms of a composite are built from the
+ * transforms of its terms).  terms/factors/blocks: k >= 1 handles.
+ *   product  terms[0] * terms[1] * ... * terms[k-1] (terms[k-1] is applied first);
+ *   sum      terms[0] + ... + terms[k-1], all the same shape;
+ *   blkdiag  block-diagonal arrangement, x split into consecutive segments;
+ *   kron     factors[0] (x) ... (x) factors[k-1] in numpy.kron order (the first
+ *            factor acts on the most significant index digit), applied as mode
+ *            products;
+ *   hermitian  A^H as an operator (forward of it is the backward of A). */
+fm_status fm_product(const fm_op* terms, int k, fm_op* out);
+fm_status fm_sum(const fm_op* terms, int k, fm_op* out);
+fm_status fm_blkdiag(const fm_op* blocks, int k, fm_op* out);
+fm_status fm_kron(const fm_op* factors, int k, fm_op* out);
+fm_status fm_hermitian(fm_op A, fm_op* out);
+
+/* ---------------------------------------------------------------- queries */
+
+fm_status fm_shape(fm_op A, int64_t* rows, int64_t* cols);
+/* 1 if every entry of A is real (real operators keep real data real). */
+fm_status fm_is_real(fm_op A, int* is_real);
+/* Element type of phi_A / beta_A output for input type `in`:
+ * complex if A or the input is complex; int8 -> int32 for FM_HAD_INT8 Hadamard;
+ * otherwise the input type.  FM_ERR_DTYPE if A does not accept `in`. */
+fm_status fm_out_dtype(fm_op A, fm_dtype in, fm_dtype* out);
+
+/* ---------------------------------------------------------------- transforms */
+
+/* Y = A X (forward, Eq. (3)) for ncols columns.  X: cols(A) x ncols block of type
+ * xdt with leading dimension ldx; Y: rows(A) x ncols block of type ydt (must equal
+ * fm_out_dtype(A, xdt)) with leading dimension ldy.  Y must not overlap X.
+ * Intermediate buffers come from a per-operator workspace that grows on demand
+ * (call fm_reserve first to keep the call free of allocation, e.g. before
+ * capturing it in a CUDA graph). */
+fm_status fm_forward(fm_op A, const void* X, int64_t ldx, fm_dtype xdt, void* Y, int64_t ldy,
+                     fm_dtype ydt, int64_t ncols, void* stream);
+
+/* X = A^H Y (backward, Eq. (4)); shapes and rules mirror fm_forward. */
+fm_status fm_backward(fm_op A, const void* Y, int64_t ldy, fm_dtype ydt, void* X, int64_t ldx,
+                      fm_dtype xdt, int64_t ncols, void* stream);
+
+/* Grow A's workspace for up to ncols columns of type xdt (both directions). */
+fm_status fm_reserve(fm_op A, int64_t ncols, fm_dtype xdt, void* stream);
+
+/* ---------------------------------------------------------------- FISTA */
+
+/* Batched FISTA (accelerated proximal gradient, cited in Sec. 3) for
+ *   min_x 1/2 ||A_i x - b_i||^2 + lambda_i ||x||_1      (Eq. (8) with tau = 2 lambda)
+ * on many independent real instances.  Per instance:
+ *   lambda = lambda_rel * ||A^T b||_inf;
+ *   L = min(safety * lam_hat, max_k |c_hat_k|^2), lam_hat = ||A v_P||^2 after P power
+ *       iterations v <- A^T A v / ||A^T A v|| from v_0 = ones / sqrt(n) (c_hat: the
+ *       spectrum of the circulant embedding of T);
+ *   x_0 = 0, y_1 = 0, t_1 = 1; for k = 1..K: g = A^T (A y_k - b),
+ *   x_k = soft(y_k - g / L, lambda / L), t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2,
+ *   y_{k+1} = x_k + (t_k - 1) / t_{k+1} (x_k - x_{k-1})    (accel = 0: y_{k+1} = x_k).
+ * FP32 state and transforms; FP64 norms, Rayleigh quotient and objective. */
+typedef struct {
+  int32_t iters;       /* K, FISTA steps (>= 0)                                       */
+  int32_t power_iters; /* P, power iterations for lam_hat (>= 1)                     */
+  double lambda_rel;   /* lambda = lambda_rel * ||A^T b||_inf                         */
+  double safety;       /* L = min(safety * lam_hat, max |c_hat|^2)                   */
+  int32_t accel;       /* 1 FISTA momentum, 0 ISTA                                    */
+  int32_t mode;        /* 0: one persistent launch over the whole batch;
+                          1: the same steps as separate per-instance launches       */
+} fm_fista_params;
+
+/* Per-instance results, DEVICE arrays of length `count` (any may be NULL):
+ * L, lambda, final objective 1/2||A x - b||^2 + lambda ||x||_1, status (0 ok,
+ * FM_ERR_NUMERIC if a non-finite value appeared). */
+typedef struct {
+  double* L;
+  double* lambda;
+  double* objective;
+  int32_t* status;
+} fm_fista_report;
+
+/* A batch of `count` instances, each A_i = Product(Partial(idx_i, n_i), Toeplitz(t_i))
+ * with real t_i (n_i x n_i, n_i a power of two in [2^4, 2^14]) and m_i selected rows;
+ * other operator shapes give FM_ERR_UNSUPPORTED.  Building the batch uploads a
+ * work list (instances sorted by size) and allocates the per-instance state. */
+fm_status fm_batch_create(const fm_op* A, int64_t count, void* stream, fm_batch* out);
+void fm_batch_release(fm_batch B);
+/* Total rows (sum m_i) and columns (sum n_i) of the batch: the lengths of the packed
+ * b and x buffers below. */
+fm_status fm_batch_sizes(fm_batch B, int64_t* total_rows, int64_t* total_cols);
+
+/* Solve every instance.  b: packed float32 measurements (instance i at offset
+ * sum_{j<i} m_j), x: packed float32 solutions (offset sum_{j<i} n_j), both device
+ * buffers.  No allocation and no host synchronisation: capturable in a CUDA graph. */
+fm_status fm_fista(fm_batch B, const float* b, float* x, const fm_fista_params* p,
+                   const fm_fista_report* rep, void* stream);
+
+/* ---------------------------------------------------------------- misc */
+
+void fm_release(fm_op A);
+const char* fm_status_string(fm_status s);
+/* Message of the last failed call on this thread ("" if none). */
+const char* fm_last_error(void);
+/* Number of kernels this library has launched in the process so far. */
+uint64_t fm_launch_count(void);
+/* Library version string. */
+const char* fm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FM_H */

@@ -1,0 +1,247 @@
+"""Structured linear operators on one GB300 GPU (the fastmat method, arXiv 1710.09578).
+
+Thin Python layer over the C ABI in ``include/fm.h``: operators are immutable handles
+built from parameter vectors (Sec. 2.1.1), composed with ``product`` / ``sum`` /
+``blkdiag`` / ``kron`` / ``.H``, and applied to blocks of columns with ``forward``
+(phi, Eq. (3)) and ``backward`` (beta, Eq. (4)).  PyTorch supplies device memory and
+the current stream only; every step of a transform runs in the library's CUDA kernels.
+
+Column blocks are torch tensors of shape ``[K, n]`` (K columns of length n, each
+contiguous) or 1-D tensors of length n.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import (FM_HAD_BF16, FM_HAD_BF16X2, FM_HAD_FP32, FM_HAD_INT8, FmError,  # noqa: F401
+                   fm_fista_params, fm_fista_report)
+
+__all__ = ["Op", "fourier", "circulant", "toeplitz", "hadamard", "diag", "partial", "product",
+           "sum_", "blkdiag", "kron", "FmApply", "apply", "FistaBatch", "FmError",
+           "FM_HAD_FP32", "FM_HAD_BF16", "FM_HAD_BF16X2", "FM_HAD_INT8", "launch_count"]
+
+_TORCH2FM = {torch.int8: _lib.FM_I8, torch.int32: _lib.FM_I32, torch.float32: _lib.FM_F32,
+             torch.float64: _lib.FM_F64, torch.complex64: _lib.FM_C64, torch.complex128: _lib.FM_C128}
+_FM2TORCH = {v: k for k, v in _TORCH2FM.items()}
+_NP2FM = {np.dtype(np.float32): _lib.FM_F32, np.dtype(np.float64): _lib.FM_F64,
+          np.dtype(np.complex64): _lib.FM_C64, np.dtype(np.complex128): _lib.FM_C128}
+
+
+def launch_count() -> int:
+    """Kernels launched by the library in this process."""
+    return _lib.fm_launch_count()
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+
+
+def _param(x, allow_int=False):
+    """(pointer, fm dtype, keep-alive) for a parameter vector in host or device memory."""
+    if isinstance(x, torch.Tensor):
+        t = x.contiguous()
+        if allow_int:
+            return t.data_ptr(), None, t
+        return t.data_ptr(), _TORCH2FM[t.dtype], t
+    a = np.ascontiguousarray(x)
+    if allow_int:
+        a = np.ascontiguousarray(a, dtype=np.int32)
+        return a.ctypes.data, None, a
+    if a.dtype.kind in "iu":
+        a = a.astype(np.float64)
+    return a.ctypes.data, _NP2FM[a.dtype], a
+
+
+class Op:
+    """An immutable structured operator (handle to the C library)."""
+
+    def __init__(self, handle: int, kids=()):
+        self._h = handle
+        self._kids = tuple(kids)  # composites also hold C references; kept for clarity
+        self.rows, self.cols = _lib.fm_shape(handle)
+        self.real = _lib.fm_is_real(handle)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            _lib.fm_release(h)
+            self._h = None
+
+    @property
+    def handle(self) -> int:
+        return self._h
+
+    @property
+    def shape(self):
+        return (self.rows, self.cols)
+
+    @property
+    def H(self) -> "Op":
+        return Op(_lib.fm_hermitian(self._h), (self,))
+
+    def out_dtype(self, dtype: torch.dtype) -> torch.dtype:
+        return _FM2TORCH[_lib.fm_out_dtype(self._h, _TORCH2FM[dtype])]
+
+    def _apply(self, X: torch.Tensor, adjoint: bool, out: torch.Tensor | None = None) -> torch.Tensor:
+        if not isinstance(X, torch.Tensor) or not X.is_cuda:
+            raise TypeError("X must be a CUDA tensor")
+        one = X.dim() == 1
+        X2 = X.unsqueeze(0) if one else X
+        if X2.dim() != 2:
+            raise ValueError("X must be [K, n] or [n]")
+        if X2.stride(-1) != 1:
+            X2 = X2.contiguous()
+        nin, nout = (self.rows, self.cols) if adjoint else (self.cols, self.rows)
+        if X2.shape[1] != nin:
+            raise ValueError(f"expected columns of length {nin}, got {X2.shape[1]}")
+        k = X2.shape[0]
+        odt = self.out_dtype(X2.dtype)
+        if out is None:
+            Y = torch.empty((k, nout), dtype=odt, device=X2.device)
+        else:
+            Y = out.view(k, nout) if out.dim() == 1 else out
+            if Y.dtype != odt or Y.stride(-1) != 1 or tuple(Y.shape) != (k, nout):
+                raise ValueError("bad output tensor")
+        ldx = X2.stride(0) if k > 1 else nin
+        ldy = Y.stride(0) if k > 1 else nout
+        fn = _lib.fm_backward if adjoint else _lib.fm_forward
+        fn(self._h, X2.data_ptr(), ldx, _TORCH2FM[X2.dtype], Y.data_ptr(), ldy, _TORCH2FM[odt], k, _stream())
+        return Y[0] if one and out is None else Y
+
+    def forward(self, X, out=None):
+        """phi_A(X) = A X (Eq. (3))."""
+        return self._apply(X, False, out)
+
+    def backward(self, Y, out=None):
+        """beta_A(Y) = A^H Y (Eq. (4))."""
+        return self._apply(Y, True, out)
+
+    def reserve(self, ncols: int, dtype: torch.dtype):
+        """Grow the workspace so that later calls on up to ncols columns allocate nothing."""
+        _lib.fm_reserve(self._h, ncols, _TORCH2FM[dtype], _stream())
+
+    def __matmul__(self, other):
+        if isinstance(other, Op):
+            return product(self, other)
+        return self.forward(other)
+
+    def __add__(self, other):
+        return sum_(self, other)
+
+
+# ---------------------------------------------------------------- constructors
+def fourier(n: int, ortho: bool = False) -> Op:
+    return Op(_lib.fm_fourier(n, 1 if ortho else 0))
+
+
+def circulant(c) -> Op:
+    p, dt, keep = _param(c)
+    return Op(_lib.fm_circulant(p, len(keep), dt, _stream()))
+
+
+def toeplitz(t, rows: int, cols: int | None = None) -> Op:
+    cols = rows if cols is None else cols
+    p, dt, keep = _param(t)
+    if len(keep) != rows + cols - 1:
+        raise ValueError("t must hold rows + cols - 1 entries")
+    return Op(_lib.fm_toeplitz(p, rows, cols, dt, _stream()))
+
+
+def hadamard(log2n: int, mode: int = FM_HAD_FP32) -> Op:
+    return Op(_lib.fm_hadamard(log2n, mode))
+
+
+def diag(d) -> Op:
+    p, dt, keep = _param(d)
+    return Op(_lib.fm_diag(p, len(keep), dt, _stream()))
+
+
+def partial(idx, n: int) -> Op:
+    if isinstance(idx, torch.Tensor):
+        idx = idx.to(torch.int32)
+    p, _, keep = _param(idx, allow_int=True)
+    return Op(_lib.fm_partial(p, len(keep), n, _stream()))
+
+
+def product(*ops: Op) -> Op:
+    return Op(_lib.fm_product([o.handle for o in ops]), ops)
+
+
+def sum_(*ops: Op) -> Op:
+    return Op(_lib.fm_sum([o.handle for o in ops]), ops)
+
+
+def blkdiag(*ops: Op) -> Op:
+    return Op(_lib.fm_blkdiag([o.handle for o in ops]), ops)
+
+
+def kron(*ops: Op) -> Op:
+    return Op(_lib.fm_kron([o.handle for o in ops]), ops)
+
+
+# ---------------------------------------------------------------- autograd
+class FmApply(torch.autograd.Function):
+    """y = A x with the hand-written adjoint as its backward: dL/dx = A^H dL/dy.
+
+    The map is linear in x, so nothing but the operator is saved; composite operators
+    (Kron, Product) recompute their intermediates inside the adjoint kernels.
+    """
+
+    @staticmethod
+    def forward(ctx, X, op: Op):
+        ctx.op = op
+        ctx.real_in = not X.is_complex()
+        return op.forward(X)
+
+    @staticmethod
+    def backward(ctx, g):
+        gx = ctx.op.backward(g.contiguous())
+        if ctx.real_in and gx.is_complex():
+            gx = gx.real.contiguous()
+        return gx, None
+
+
+def apply(op: Op, X: torch.Tensor) -> torch.Tensor:
+    """Differentiable A X."""
+    return FmApply.apply(X, op)
+
+
+# ---------------------------------------------------------------- FISTA
+class FistaBatch:
+    """Many independent instances A_i = P_i T_i solved together (``fm_fista``)."""
+
+    def __init__(self, ops):
+        self.ops = list(ops)
+        self._b = _lib.fm_batch_create([o.handle for o in self.ops], _stream())
+        self.total_rows, self.total_cols = _lib.fm_batch_sizes(self._b)
+        self.count = len(self.ops)
+
+    def __del__(self):
+        b = getattr(self, "_b", None)
+        if b:
+            _lib.fm_batch_release(b)
+            self._b = None
+
+    def solve(self, b: torch.Tensor, x: torch.Tensor | None = None, iters: int = 200, power_iters: int = 20,
+              lambda_rel: float = 0.01, safety: float = 1.05, accel: bool = True, mode: int = 0,
+              report: bool = False):
+        if b.dtype != torch.float32 or not b.is_cuda or b.numel() != self.total_rows:
+            raise ValueError("b must be a packed float32 CUDA tensor of the batch's total rows")
+        if x is None:
+            x = torch.empty(self.total_cols, dtype=torch.float32, device=b.device)
+        params = fm_fista_params(iters, power_iters, lambda_rel, safety, 1 if accel else 0, mode)
+        rep = None
+        out = None
+        if report:
+            out = {"L": torch.empty(self.count, dtype=torch.float64, device=b.device),
+                   "lambda": torch.empty(self.count, dtype=torch.float64, device=b.device),
+                   "objective": torch.empty(self.count, dtype=torch.float64, device=b.device),
+                   "status": torch.empty(self.count, dtype=torch.int32, device=b.device)}
+            rep = fm_fista_report(out["L"].data_ptr(), out["lambda"].data_ptr(),
+                                  out["objective"].data_ptr(), out["status"].data_ptr())
+        _lib.fm_fista(self._b, b.data_ptr(), x.data_ptr(), params, rep, _stream())
+        return (x, out) if report else x

@@ -1,0 +1,361 @@
+// Batched Stockham FFT engine for the Fourier, Circulant and Toeplitz operators.
+//
+// One CTA owns a tile of V vectors of length L (L * V = THREADS * EPT elements) in
+// shared memory and runs radix-8/4/2 Stockham passes over it: each thread keeps EPT
+// elements in registers, multiplies by the twiddles of the pass, does the small DFT in
+// registers and writes the results to their auto-sorted place, so no bit reversal is
+// ever needed (the DFT of Eq. (1), evaluated by the butterfly factorisation the paper
+// mentions in Sec. 1).  For a circulant or Toeplitz operator the forward transform, the
+// multiplication by the precomputed spectrum (Eq. (5); Sec. 2.1.1) and the inverse
+// transform all run in the same CTA: the last forward pass and the first inverse pass
+// touch the same elements, so the spectrum product happens in registers.
+//
+// Vectors are read through a general strided view so that one kernel serves plain
+// column blocks, mode products of Kron (the transform runs along one axis of the column
+// seen as [outer][L][inner]) and the two-pass plan for long transforms.  Diag and row
+// selection (P, P^H) neighbours of a Product, zero-padding and truncation for the
+// Toeplitz embedding, twiddles of the two-pass plan, scaling and accumulation (for Sum)
+// are fused into the loads and stores.
+#pragma once
+#include "fft.h"
+#include "fm_device.cuh"
+#include "fm_internal.h"
+
+namespace fm {
+
+// Per-vector addressing, computed once per tile into shared memory.
+struct VecInfo {
+  int64_t in_off;   // element offset of t = 0 (column 2c in IO_RP mode); -1: vector absent
+  int64_t out_off;
+  int32_t in_n2;    // ((o*inner + i) / in_fdiv) % in_fmod
+  int32_t out_n2;
+  int32_t tw_n2;    // ((o*inner + i) / tw_div) % tw_mod
+  int32_t flags;    // bit 0: second real column of a pair exists
+  int64_t soff;     // spectrum row offset
+};
+
+template <typename T>
+__device__ __forceinline__ typename Cx<T>::t fft_load(const FftArgs<T>& a, const VecInfo& vi, int t) {
+  typedef typename Cx<T>::t C;
+  if (vi.in_off < 0) return cmake((T)0, (T)0);
+  const int64_t n = (int64_t)t * a.in_fmul + vi.in_n2;
+  if (n >= a.Lin) return cmake((T)0, (T)0);
+  int64_t src = n;
+  if (a.pre_map) {
+    src = a.pre_map[n];
+    if (src < 0) return cmake((T)0, (T)0);
+  }
+  const int64_t off = vi.in_off + src * a.in_tstride;
+  C x;
+  if (a.in_mode == IO_C) {
+    x = reinterpret_cast<const C*>(a.in)[off];
+  } else {
+    const T* p = reinterpret_cast<const T*>(a.in);
+    T re = p[off];
+    T im = (a.in_mode == IO_RP && (vi.flags & 1)) ? p[off + a.in_ld] : (T)0;
+    x = cmake(re, im);
+  }
+  if (a.pre_dc) {
+    C d = a.pre_dc[n];
+    x = cmul(x, a.pre_conj ? cconj(d) : d);
+  } else if (a.pre_dr) {
+    x = cscale(x, a.pre_dr[n]);
+  }
+  if (a.pre_tw) {
+    C w = a.pre_tw[((int64_t)t * vi.tw_n2) & a.tw_mask];
+    x = cmul(x, a.pre_tw_conj ? cconj(w) : w);
+  }
+  return x;
+}
+
+template <typename T>
+__device__ __forceinline__ void fft_store(const FftArgs<T>& a, const VecInfo& vi, int t, typename Cx<T>::t x) {
+  typedef typename Cx<T>::t C;
+  if (vi.out_off < 0) return;
+  if (a.post_tw) {
+    C w = a.post_tw[((int64_t)t * vi.tw_n2) & a.tw_mask];
+    x = cmul(x, a.post_tw_conj ? cconj(w) : w);
+  }
+  const int64_t n = (int64_t)t * a.out_fmul + vi.out_n2;
+  if (n >= a.Lout) return;
+  if (a.post_dc) {
+    C d = a.post_dc[n];
+    x = cmul(x, a.post_conj ? cconj(d) : d);
+  } else if (a.post_dr) {
+    x = cscale(x, a.post_dr[n]);
+  }
+  x = cscale(x, a.scale);
+  int64_t dst = n;
+  if (a.post_map) {
+    dst = a.post_map[n];
+    if (dst < 0) return;
+  }
+  const int64_t off = vi.out_off + dst * a.out_tstride;
+  if (a.out_mode == IO_C) {
+    C* p = reinterpret_cast<C*>(a.out) + off;
+    if (a.beta) x = cadd(x, *p);
+    *p = x;
+  } else {
+    T* p = reinterpret_cast<T*>(a.out) + off;
+    *p = a.beta ? x.x + *p : x.x;
+    if (a.out_mode == IO_RP && (vi.flags & 1)) {
+      p += a.out_ld;
+      *p = a.beta ? x.y + *p : x.y;
+    }
+  }
+}
+
+template <int R> struct LogR { static constexpr int v = R == 8 ? 3 : (R == 4 ? 2 : 1); };
+
+// Butterfly b = tid + q*THREADS of a radix-R pass covers vector v and index j in [0, L/R);
+// its R inputs are t = j + k L/R.
+__device__ __forceinline__ void bfly_coords(int b, int logV, int logLR, int vfast, int& j, int& v) {
+  if (vfast) {
+    v = b & ((1 << logV) - 1);
+    j = b >> logV;
+  } else {
+    j = b & ((1 << logLR) - 1);
+    v = b >> logLR;
+  }
+}
+
+__device__ __forceinline__ int lin_index(int t, int v, int logL, int logV, int vfast) {
+  return vfast ? ((t << logV) + v) : ((v << logL) + t);
+}
+
+// Load the R inputs t = j + k L/R of each of this thread's butterflies.
+template <int R, int THREADS, int EPT, typename C>
+__device__ __forceinline__ void regs_from_smem(C (&r)[EPT], const C* s, int logL, int logV, int vfast) {
+  const int logLR = logL - LogR<R>::v;
+#pragma unroll
+  for (int q = 0; q < EPT / R; ++q) {
+    int j, v;
+    bfly_coords(threadIdx.x + q * THREADS, logV, logLR, vfast, j, v);
+#pragma unroll
+    for (int k = 0; k < R; ++k) r[q * R + k] = s[spad(lin_index(j + (k << logLR), v, logL, logV, vfast))];
+  }
+}
+
+// Store the outputs of a radix-R pass to their Stockham positions (j/Ns) Ns R + j%Ns + k Ns.
+// For the last pass (Ns R = L) these are the natural positions j + k L/R.
+template <int R, int THREADS, int EPT, typename C>
+__device__ __forceinline__ void regs_to_smem(const C (&r)[EPT], C* s, int logL, int logV, int vfast, int logNs) {
+  const int logR = LogR<R>::v;
+  const int logLR = logL - logR;
+#pragma unroll
+  for (int q = 0; q < EPT / R; ++q) {
+    int j, v;
+    bfly_coords(threadIdx.x + q * THREADS, logV, logLR, vfast, j, v);
+    const int jm = j & ((1 << logNs) - 1);
+    const int base = ((j >> logNs) << (logNs + logR)) + jm;
+#pragma unroll
+    for (int k = 0; k < R; ++k) s[spad(lin_index(base + (k << logNs), v, logL, logV, vfast))] = r[q * R + k];
+  }
+}
+
+// Twiddle W_{Ns R}^{dir k jm} then DFT_R, for each butterfly of this thread.
+template <int R, int THREADS, int EPT, typename C>
+__device__ __forceinline__ void pass_compute(C (&r)[EPT], int logL, int logV, int vfast, int logNs, int dir,
+                                             const C* __restrict__ tw) {
+  const int logR = LogR<R>::v;
+  const int logLR = logL - logR;
+#pragma unroll
+  for (int q = 0; q < EPT / R; ++q) {
+    int j, v;
+    bfly_coords(threadIdx.x + q * THREADS, logV, logLR, vfast, j, v);
+    if (logNs > 0) {
+      const int jm = j & ((1 << logNs) - 1);
+      C w = tw[jm << (kTwLog - logNs - logR)];
+      if (dir > 0) w = cconj(w);
+      C wk = w;
+#pragma unroll
+      for (int k = 1; k < R; ++k) {
+        r[q * R + k] = cmul(r[q * R + k], wk);
+        if (k + 1 < R) wk = cmul(wk, w);
+      }
+    }
+    if (R == 8) dft8(&r[q * R], dir);
+    else if (R == 4) dft4(&r[q * R], dir);
+    else dft2(&r[q * R]);
+  }
+}
+
+// Spectrum product at the natural positions t = j + k L/R of the last forward pass.
+template <int R, int THREADS, int EPT, typename C>
+__device__ __forceinline__ void spec_mul(C (&r)[EPT], const C* __restrict__ spec, int conj, const VecInfo* vinfo,
+                                         int logL, int logV, int vfast) {
+  const int logLR = logL - LogR<R>::v;
+#pragma unroll
+  for (int q = 0; q < EPT / R; ++q) {
+    int j, v;
+    bfly_coords(threadIdx.x + q * THREADS, logV, logLR, vfast, j, v);
+    const C* sp = spec + vinfo[v].soff + j;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      C w = sp[k << logLR];
+      r[q * R + k] = cmul(r[q * R + k], conj ? cconj(w) : w);
+    }
+  }
+}
+
+#define FM_RADIX_SWITCH(R, CALL) \
+  switch (R) {                   \
+    case 8: { CALL(8); } break;  \
+    case 4: { CALL(4); } break;  \
+    default: { CALL(2); } break; \
+  }
+
+template <typename T, int THREADS, int EPT>
+__global__ void __launch_bounds__(THREADS) fft_tile_kernel(const __grid_constant__ FftArgs<T> a) {
+  typedef typename Cx<T>::t C;
+  constexpr int E = THREADS * EPT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* s = reinterpret_cast<C*>(smem_raw);
+  VecInfo* vinfo = reinterpret_cast<VecInfo*>(smem_raw + (size_t)(E + E / 16 + 1) * sizeof(C));
+  const int logL = a.logL, logV = a.logV, vfast = a.vfast, V = a.V;
+  const int64_t g0 = (int64_t)blockIdx.x * V;
+  const int64_t nvec = a.ncu * a.outer * a.inner;
+
+  // ---- per-vector addressing
+  for (int v = threadIdx.x; v < V; v += THREADS) {
+    VecInfo vi;
+    const int64_t g = g0 + v;
+    if (g < nvec) {
+      const int64_t i = g % a.inner, q = g / a.inner;
+      const int64_t o = q % a.outer, c = q / a.outer;
+      const int64_t oi = o * a.inner + i;
+      const int64_t cin = a.in_mode == IO_RP ? 2 * c : c;
+      const int64_t cout = a.out_mode == IO_RP ? 2 * c : c;
+      vi.in_off = cin * a.in_ld + o * a.in_ostride + (i % a.in_imod);
+      vi.out_off = cout * a.out_ld + o * a.out_ostride + (i % a.out_imod);
+      vi.in_n2 = (int32_t)((oi / a.in_fdiv) % a.in_fmod);
+      vi.out_n2 = (int32_t)((oi / a.out_fdiv) % a.out_fmod);
+      vi.tw_n2 = (int32_t)((oi / a.tw_div) % a.tw_mod);
+      vi.flags = (2 * c + 1 < a.ncols) ? 1 : 0;
+      vi.soff = a.spec_omod > 1 ? ((o % a.spec_omod) << logL) : 0;
+    } else {
+      vi.in_off = -1;
+      vi.out_off = -1;
+      vi.in_n2 = vi.out_n2 = vi.tw_n2 = 0;
+      vi.flags = 0;
+      vi.soff = 0;
+    }
+    vinfo[v] = vi;
+  }
+  __syncthreads();
+
+  // ---- load, staged through shared memory in the order that is contiguous in HBM
+  for (int e = threadIdx.x; e < E; e += THREADS) {
+    int t, v;
+    if (a.in_vcontig) { v = e & (V - 1); t = e >> logV; }
+    else { t = e & ((1 << logL) - 1); v = e >> logL; }
+    s[spad(lin_index(t, v, logL, logV, vfast))] = fft_load<T>(a, vinfo[v], t);
+  }
+  __syncthreads();
+
+  C r[EPT];
+  const int R0 = a.rad[0];
+#define LS(RR) regs_from_smem<RR, THREADS, EPT, C>(r, s, logL, logV, vfast)
+  FM_RADIX_SWITCH(R0, LS)
+
+  // ---- passes: forward (dir0) and, for a convolution, spectrum product + inverse
+  int Rlast = R0;
+  const int nseg = a.conv ? 2 : 1;
+  for (int seg = 0; seg < nseg; ++seg) {
+    const int dir = seg == 0 ? a.dir0 : -a.dir0;
+    int logNs = 0;
+    for (int p = 0; p < a.nrad; ++p) {
+      const int R = seg == 0 ? a.rad[p] : a.rad[a.nrad - 1 - p];
+#define PC(RR) pass_compute<RR, THREADS, EPT, C>(r, logL, logV, vfast, logNs, dir, a.tw)
+      FM_RADIX_SWITCH(R, PC)
+#undef PC
+      Rlast = R;
+      if (p + 1 == a.nrad) break;
+      __syncthreads();
+#define PS(RR) regs_to_smem<RR, THREADS, EPT, C>(r, s, logL, logV, vfast, logNs)
+      FM_RADIX_SWITCH(R, PS)
+#undef PS
+      __syncthreads();
+      const int Rn = seg == 0 ? a.rad[p + 1] : a.rad[a.nrad - 2 - p];
+      FM_RADIX_SWITCH(Rn, LS)
+      logNs += (R == 8 ? 3 : (R == 4 ? 2 : 1));
+    }
+    if (seg == 0 && a.conv) {
+#define SPM(RR) spec_mul<RR, THREADS, EPT, C>(r, a.spec, a.spec_conj, vinfo, logL, logV, vfast)
+      FM_RADIX_SWITCH(Rlast, SPM)
+#undef SPM
+    }
+  }
+#undef LS
+
+  // ---- store, staged through shared memory
+  __syncthreads();
+  const int logLast = logL - (Rlast == 8 ? 3 : (Rlast == 4 ? 2 : 1));
+#define ST(RR) regs_to_smem<RR, THREADS, EPT, C>(r, s, logL, logV, vfast, logLast)
+  FM_RADIX_SWITCH(Rlast, ST)
+#undef ST
+  __syncthreads();
+  for (int e = threadIdx.x; e < E; e += THREADS) {
+    int t, v;
+    if (a.out_vcontig) { v = e & (V - 1); t = e >> logV; }
+    else { t = e & ((1 << logL) - 1); v = e >> logL; }
+    fft_store<T>(a, vinfo[v], t, s[spad(lin_index(t, v, logL, logV, vfast))]);
+  }
+}
+
+// ------------------------------------------------------------------ host side
+template <typename T, int THREADS, int EPT>
+static fm_status launch_cfg(FftArgs<T> a, cudaStream_t st) {
+  typedef typename Cx<T>::t C;
+  constexpr int E = THREADS * EPT;
+  a.V = (int)(E >> a.logL);
+  a.logV = 0;
+  while ((1 << a.logV) < a.V) ++a.logV;
+  const int64_t nvec = a.ncu * a.outer * a.inner;
+  const int64_t tiles = (nvec + a.V - 1) / a.V;
+  if (tiles > 0x7fffffffLL) { set_error("fft: too many tiles"); return FM_ERR_UNSUPPORTED; }
+  // vectors adjacent in HBM: consecutive inner index, or unit outer stride
+  a.in_vcontig = (a.inner > 1 || a.in_ostride == 1) ? 1 : 0;
+  a.out_vcontig = (a.inner > 1 || a.out_ostride == 1) ? 1 : 0;
+  // passes run with vectors fastest when a tile holds enough of them
+  a.vfast = a.V >= 16 ? 1 : 0;
+  const size_t smem = (size_t)(E + E / 16 + 1) * sizeof(C) + (size_t)a.V * sizeof(VecInfo);
+  auto kern = fft_tile_kernel<T, THREADS, EPT>;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  static std::atomic<unsigned long long> attr_bytes[32];
+  if (dev < 32 && attr_bytes[dev].load() < smem) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) { set_error("fft smem attribute: %s", cudaGetErrorString(e)); return FM_ERR_CUDA; }
+    attr_bytes[dev].store(smem);
+  }
+  kern<<<(unsigned)tiles, THREADS, smem, st>>>(a);
+  return after_launch("fft_tile_kernel");
+}
+
+template <typename T>
+int fft_max_tile() { return sizeof(T) == 4 ? 16384 : 8192; }
+
+template <typename T>
+fm_status fft_launch(FftArgs<T> a, cudaStream_t st) {
+  if (a.L < 2 || (a.L & (a.L - 1)) || a.L > fft_max_tile<T>()) {
+    set_error("fft: unsupported single-tile length %lld", (long long)a.L);
+    return FM_ERR_UNSUPPORTED;
+  }
+  a.logL = 0;
+  while ((1LL << a.logL) < a.L) ++a.logL;
+  // radix schedule: 8s, then one 4 or 2
+  a.nrad = 0;
+  int rem = a.logL;
+  while (rem >= 3) { a.rad[a.nrad++] = 8; rem -= 3; }
+  if (rem == 2) a.rad[a.nrad++] = 4;
+  if (rem == 1) a.rad[a.nrad++] = 2;
+  if (a.ncu * a.outer * a.inner == 0) return FM_OK;
+  if (a.L <= 4096) return launch_cfg<T, 256, 16>(a, st);
+  if (a.L <= 8192) return launch_cfg<T, 512, 16>(a, st);
+  if constexpr (sizeof(T) == 4) return launch_cfg<T, 512, 32>(a, st);
+  set_error("fft: length %lld", (long long)a.L);
+  return FM_ERR_UNSUPPORTED;
+}
+
+}  // namespace fm

@@ -1,0 +1,139 @@
+// Internal declarations of the structured-operator library (host side).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <cstdio>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/fm.h"
+
+namespace fm {
+
+// ------------------------------------------------------------------ errors
+void set_error(const char* fmt, ...);
+void clear_error();
+
+#define FM_TRY(expr)                          \
+  do {                                        \
+    fm_status _s = (expr);                    \
+    if (_s != FM_OK) return _s;               \
+  } while (0)
+
+#define FM_CUDA(expr)                                                             \
+  do {                                                                            \
+    cudaError_t _e = (expr);                                                      \
+    if (_e != cudaSuccess) {                                                      \
+      ::fm::set_error("%s:%d %s: %s", __FILE__, __LINE__, #expr,                  \
+                      cudaGetErrorString(_e));                                    \
+      return _e == cudaErrorMemoryAllocation ? FM_ERR_OOM : FM_ERR_CUDA;          \
+    }                                                                             \
+  } while (0)
+
+// Every kernel launch of the library goes through this counter.
+extern std::atomic<uint64_t> g_launches;
+inline fm_status after_launch(const char* what) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error("launch of %s failed: %s", what, cudaGetErrorString(e));
+    return FM_ERR_CUDA;
+  }
+  return FM_OK;
+}
+
+// ------------------------------------------------------------------ dtypes
+inline bool is_complex(fm_dtype d) { return d == FM_C64 || d == FM_C128; }
+inline bool is_double(fm_dtype d) { return d == FM_F64 || d == FM_C128; }
+inline int dtype_size(fm_dtype d) {
+  switch (d) {
+    case FM_I8: return 1;
+    case FM_I32: return 4;
+    case FM_F32: return 4;
+    case FM_F64: return 8;
+    case FM_C64: return 8;
+    case FM_C128: return 16;
+  }
+  return 0;
+}
+inline fm_dtype complex_of(fm_dtype d) {
+  if (d == FM_F32) return FM_C64;
+  if (d == FM_F64) return FM_C128;
+  return d;
+}
+
+// ------------------------------------------------------------------ per-device tables
+// W_{kTwMax}^m = exp(-2 pi i m / kTwMax), m in [0, kTwMax), in FP32 and FP64, computed once
+// per device in FP64 with sincospi.
+constexpr int kTwLog = 14;
+constexpr int kTwMax = 1 << kTwLog;
+struct DeviceTables {
+  float2* tw32 = nullptr;
+  double2* tw64 = nullptr;
+};
+fm_status device_tables(int device, DeviceTables** out);
+
+// ------------------------------------------------------------------ operators
+enum OpKind {
+  K_FOURIER, K_CIRCULANT, K_TOEPLITZ, K_HADAMARD, K_DIAG, K_PARTIAL,
+  K_PRODUCT, K_SUM, K_BLKDIAG, K_KRON, K_HERMITIAN
+};
+
+// Twiddles and spectra for a length-L transform done in two passes (L = N1 * N2).
+struct BigPlan {
+  int64_t L = 0, N1 = 0, N2 = 0;
+  float2* tw32 = nullptr;   // W_L^m, m in [0, L)
+  double2* tw64 = nullptr;
+};
+
+struct Workspace {
+  std::mutex mu;
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  int device = -1;
+};
+
+}  // namespace fm
+
+struct fm_op_s {
+  std::atomic<int> refs{1};
+  fm::OpKind kind;
+  int64_t rows = 0, cols = 0;
+  bool real = true;
+  int device = 0;
+  // leaf parameters
+  int ortho = 0;                 // Fourier
+  int log2n = 0;                 // Hadamard
+  fm_had_mode had_mode = FM_HAD_FP32;
+  int64_t L = 0;                 // transform length (Fourier n, circulant n, Toeplitz embedding)
+  // circulant / Toeplitz spectrum of the embedding, already divided by L
+  // (natural order, and the row-permuted copy used by the two-pass plan)
+  double2* spec64 = nullptr;
+  float2* spec32 = nullptr;
+  double2* spec64_perm = nullptr;
+  float2* spec32_perm = nullptr;
+  double cap = 0.0;              // max |spectrum * L|^2 (FISTA step cap)
+  // diagonal
+  double2* d64 = nullptr;        // complex diagonal (both precisions) ...
+  float2* d32 = nullptr;
+  double* dr64 = nullptr;        // ... or real diagonal
+  float* dr32 = nullptr;
+  // row selection
+  int32_t* idx = nullptr;        // m selected rows
+  int32_t* inv = nullptr;        // n entries: r if idx[r] == j, else -1
+  std::vector<int32_t> idx_host;
+  // two-pass plan for long transforms
+  fm::BigPlan big;
+  // composites
+  std::vector<fm_op_s*> kids;
+  fm::Workspace ws;
+};
+
+namespace fm {
+void op_retain(fm_op_s* A);
+void op_release(fm_op_s* A);
+}  // namespace fm

@@ -1,0 +1,209 @@
+// Fast Walsh-Hadamard transform for the Sylvester Hadamard operator (CUDA-core paths).
+//
+// H_n = H_2 (x) H_2 (x) ... (x) H_2 in natural order, H[i, j] = (-1)^popcount(i & j),
+// so the transform is a sequence of +- butterflies, one per index bit, in any order.
+// A CTA holds a tile of V vectors of length Lp in shared memory and applies in-place
+// radix-16 passes (four bits per pass, done in registers).  A column longer than one tile
+// (n = C * Lp) is split by its C top index values: with x = [x_0; ...; x_{C-1}] the output
+// block r is H_Lp (sum_s H_C[r, s] x_s), so CTA r combines the C input blocks while
+// loading and transforms its own block; the C CTAs of a column read the same lines at
+// the same time, so HBM sees each input byte about once.
+//
+// Element types: f32 -> f32, c64 -> c64 (as two real channels), int8 -> int32 (exact).
+#include "fm_device.cuh"
+#include "fm_internal.h"
+#include "fwht.h"
+
+namespace fm {
+
+__device__ __forceinline__ float wadd(float a, float b) { return a + b; }
+__device__ __forceinline__ float wsub(float a, float b) { return a - b; }
+__device__ __forceinline__ int wadd(int a, int b) { return a + b; }
+__device__ __forceinline__ int wsub(int a, int b) { return a - b; }
+__device__ __forceinline__ float2 wadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 wsub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+template <typename W> __device__ __forceinline__ W wzero();
+template <> __device__ __forceinline__ float wzero<float>() { return 0.f; }
+template <> __device__ __forceinline__ int wzero<int>() { return 0; }
+template <> __device__ __forceinline__ float2 wzero<float2>() { return make_float2(0.f, 0.f); }
+
+template <typename Tin, typename W> __device__ __forceinline__ W wload(const Tin* p);
+template <> __device__ __forceinline__ float wload<float, float>(const float* p) { return *p; }
+template <> __device__ __forceinline__ float2 wload<float2, float2>(const float2* p) { return *p; }
+template <> __device__ __forceinline__ int wload<int8_t, int>(const int8_t* p) { return (int)*p; }
+
+template <typename W, int R>
+__device__ __forceinline__ void wht_regs(W* x) {
+#pragma unroll
+  for (int h = 1; h < R; h <<= 1) {
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      if ((i & h) == 0) {
+        W a = x[i], b = x[i + h];
+        x[i] = wadd(a, b);
+        x[i + h] = wsub(a, b);
+      }
+    }
+  }
+}
+
+// One in-place pass over index bits [sh, sh + RB) of every vector in the tile.
+template <typename W, int RB, int THREADS, int E>
+__device__ __forceinline__ void wht_pass(W* s, int sh, int logLp, int logV, int vfast) {
+  constexpr int R = 1 << RB;
+  const int V = 1 << logV;
+  for (int b = threadIdx.x; b < (E >> RB); b += THREADS) {
+    int v, lo, hi;
+    if (vfast) {
+      v = b & (V - 1);
+      const int rest = b >> logV;
+      lo = rest & ((1 << sh) - 1);
+      hi = rest >> sh;
+    } else {
+      lo = b & ((1 << sh) - 1);
+      const int rest = b >> sh;
+      const int nhi_log = logLp - sh - RB;
+      hi = rest & ((1 << nhi_log) - 1);
+      v = rest >> nhi_log;
+    }
+    const int t0 = (hi << (sh + RB)) + lo;
+    W x[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int t = t0 + (k << sh);
+      x[k] = s[spad(vfast ? ((t << logV) + v) : ((v << logLp) + t))];
+    }
+    wht_regs<W, R>(x);
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int t = t0 + (k << sh);
+      s[spad(vfast ? ((t << logV) + v) : ((v << logLp) + t))] = x[k];
+    }
+  }
+}
+
+struct WVec {
+  int64_t in_off;   // -1 if absent
+  int64_t out_off;
+};
+
+template <typename Tin, typename W, typename Tout, int THREADS, int EPT>
+__global__ void __launch_bounds__(THREADS) fwht_tile_kernel(const __grid_constant__ FwhtArgs a) {
+  constexpr int E = THREADS * EPT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  W* s = reinterpret_cast<W*>(smem_raw);
+  WVec* vinfo = reinterpret_cast<WVec*>(smem_raw + (size_t)(E + E / 16 + 1) * sizeof(W));
+  const int logLp = a.logLp, logV = a.logV, V = 1 << a.logV;
+  const int C = 1 << a.logC;
+  // blockIdx.x = tile * C + part
+  const int part = (int)(blockIdx.x & (C - 1));
+  const int64_t tile = (int64_t)blockIdx.x >> a.logC;
+  const int64_t g0 = tile * V;
+  const int64_t nvec = a.ncols * a.outer * a.inner;
+  const int vfast = V >= 16;
+
+  for (int v = threadIdx.x; v < V; v += THREADS) {
+    WVec vi;
+    const int64_t g = g0 + v;
+    if (g < nvec) {
+      const int64_t i = g % a.inner, q = g / a.inner;
+      const int64_t o = q % a.outer, c = q / a.outer;
+      vi.in_off = c * a.in_ld + o * a.in_ostride + i;
+      vi.out_off = c * a.out_ld + o * a.out_ostride + i;
+    } else {
+      vi.in_off = -1;
+      vi.out_off = -1;
+    }
+    vinfo[v] = vi;
+  }
+  __syncthreads();
+
+  const Tin* in = reinterpret_cast<const Tin*>(a.in);
+  Tout* out = reinterpret_cast<Tout*>(a.out);
+  const int64_t Lp = (int64_t)1 << logLp;
+  // ---- load and combine the C blocks with row `part` of H_C
+  for (int e = threadIdx.x; e < E; e += THREADS) {
+    int t, v;
+    if (vfast) { v = e & (V - 1); t = e >> logV; }
+    else { t = e & ((1 << logLp) - 1); v = e >> logLp; }
+    const WVec vi = vinfo[v];
+    W acc = wzero<W>();
+    if (vi.in_off >= 0) {
+      for (int sblk = 0; sblk < C; ++sblk) {
+        W x = wload<Tin, W>(in + vi.in_off + ((int64_t)sblk * Lp + t) * a.in_tstride);
+        acc = (__popc(sblk & part) & 1) ? wsub(acc, x) : wadd(acc, x);
+      }
+    }
+    s[spad(vfast ? ((t << logV) + v) : ((v << logLp) + t))] = acc;
+  }
+  __syncthreads();
+
+  // ---- in-place passes, up to four bits each
+  for (int sh = 0; sh < logLp; sh += 4) {
+    const int rb = min(4, logLp - sh);
+    switch (rb) {
+      case 4: wht_pass<W, 4, THREADS, E>(s, sh, logLp, logV, vfast); break;
+      case 3: wht_pass<W, 3, THREADS, E>(s, sh, logLp, logV, vfast); break;
+      case 2: wht_pass<W, 2, THREADS, E>(s, sh, logLp, logV, vfast); break;
+      default: wht_pass<W, 1, THREADS, E>(s, sh, logLp, logV, vfast); break;
+    }
+    __syncthreads();
+  }
+
+  // ---- store block `part`
+  for (int e = threadIdx.x; e < E; e += THREADS) {
+    int t, v;
+    if (vfast) { v = e & (V - 1); t = e >> logV; }
+    else { t = e & ((1 << logLp) - 1); v = e >> logLp; }
+    const WVec vi = vinfo[v];
+    if (vi.out_off < 0) continue;
+    W y = s[spad(vfast ? ((t << logV) + v) : ((v << logLp) + t))];
+    Tout* p = out + vi.out_off + ((int64_t)part * Lp + t) * a.out_tstride;
+    if (a.beta) y = wadd(y, *p);
+    *p = y;
+  }
+}
+
+template <typename Tin, typename W, typename Tout, int THREADS, int EPT>
+static fm_status fwht_cfg(FwhtArgs a, cudaStream_t st) {
+  constexpr int E = THREADS * EPT;
+  // tile: Lp = min(L, E) elements per vector, V = E / Lp vectors, C = L / Lp parts
+  int logE = 0;
+  while ((1 << logE) < E) ++logE;
+  a.logLp = a.logL < logE ? a.logL : logE;
+  a.logC = a.logL - a.logLp;
+  a.logV = logE - a.logLp;
+  if (a.logC > 4) { set_error("fwht: length 2^%d too long", a.logL); return FM_ERR_UNSUPPORTED; }
+  const int64_t nvec = a.ncols * a.outer * a.inner;
+  const int64_t tiles = (nvec + (1 << a.logV) - 1) >> a.logV;
+  const int64_t blocks = tiles << a.logC;
+  if (blocks > 0x7fffffffLL) { set_error("fwht: too many tiles"); return FM_ERR_UNSUPPORTED; }
+  const size_t smem = (size_t)(E + E / 16 + 1) * sizeof(W) + ((size_t)1 << a.logV) * sizeof(WVec);
+  auto kern = fwht_tile_kernel<Tin, W, Tout, THREADS, EPT>;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  static std::atomic<unsigned long long> attr_bytes[32];
+  if (dev < 32 && attr_bytes[dev].load() < smem) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) { set_error("fwht smem attribute: %s", cudaGetErrorString(e)); return FM_ERR_CUDA; }
+    attr_bytes[dev].store(smem);
+  }
+  if (blocks == 0) return FM_OK;
+  kern<<<(unsigned)blocks, THREADS, smem, st>>>(a);
+  return after_launch("fwht_tile_kernel");
+}
+
+fm_status fwht_launch(FwhtArgs a, fm_dtype in_dt, cudaStream_t st) {
+  if (a.logL < 1) { set_error("fwht: n must be >= 2"); return FM_ERR_UNSUPPORTED; }
+  switch (in_dt) {
+    case FM_F32: return fwht_cfg<float, float, float, 512, 32>(a, st);
+    case FM_C64: return fwht_cfg<float2, float2, float2, 512, 16>(a, st);
+    case FM_I8: return fwht_cfg<int8_t, int, int, 512, 32>(a, st);
+    default: break;
+  }
+  set_error("fwht: dtype %d not supported", (int)in_dt);
+  return FM_ERR_DTYPE;
+}
+
+}  // namespace fm
