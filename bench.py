@@ -1,0 +1,346 @@
+"""Throughput of the structured-operator hot path on GB300 (one JSON line on stdout).
+
+Step = forward + adjoint of the Sylvester Hadamard operator (n = 2^16) on a block of
+256 FP32 columns (64 MiB in, 64 MiB out per apply), the workload the headline metric is
+quoted on.  ``value`` is whole-job GB/s of algorithmic bytes (read X + write Y per apply)
+with inputs resident in HBM; L2 is flushed (a 2x-L2 memset) before every timed step and
+only the two applies are inside the events.  ``e2e`` is the same metric through the
+public API with pinned HOST buffers: H2D of X, forward, adjoint, D2H of the result.
+
+Other rows of the hot path (int8 / BF16 Hadamard, the compressed-sensing operator
+P Diag(d) C at 2^18, the Kron(H, C, F) operator at 2^24, the complex128 circulant, and
+batched FISTA solves/s) are reported under ``"rows"``.
+
+``--impl reference`` times the FP64 CPU oracle on the same metric (bounded sample).
+Multi-GPU: replicas only -- each rank runs its own block, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import fm_inputs as I  # noqa: E402
+
+LOG2N = 16
+NCOLS = 256
+N = 1 << LOG2N
+APPLY_BYTES = 2 * N * NCOLS * 4            # read X + write Y, FP32
+STEP_BYTES = 2 * APPLY_BYTES               # forward + adjoint
+METRIC = "fwd+adjoint apply GB/s vs HBM peak; batched FISTA solves/s at 1e-4 rel err"
+WORKLOAD = "Sylvester Hadamard n=2^16, 256 FP32 columns, forward + adjoint"
+# DRAM bytes of one fwht_tile_kernel launch on this workload, from the ncu capture
+# summarised in profiles/fwht_tile_kernel_hadamard_2p16x256.md (None until captured).
+NCU_TRAFFIC = None
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reference_arm(args, world, rank):
+    """FP64 CPU oracle on the same metric, bounded sample of columns per step."""
+    if rank != 0:
+        return
+    import oracle as O
+    xf, _ = I.hadamard_block()
+    cols = 4
+    H = O.Hadamard(N)
+    X = xf[:cols].T.astype(np.float64)
+    for _ in range(args.warmup):
+        H.apply(H.apply(X), adjoint=True)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        Y = H.apply(X)
+        H.apply(Y, adjoint=True)
+    dt = time.perf_counter() - t0
+    sample_bytes = 2 * 2 * N * cols * 4
+    gbs = sample_bytes * args.steps / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n": N, "columns": NCOLS},
+            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{cols} of {NCOLS} columns per step, FP64 numpy butterflies"},
+            "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline():
+    """The oracle as it stands on the host cores: about 10 s on a bounded column sample."""
+    import oracle as O
+    xf, _ = I.hadamard_block(k=8)
+    H = O.Hadamard(N)
+    X = xf.T.astype(np.float64)
+    reps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < 10.0:
+        Y = H.apply(X)
+        H.apply(Y, adjoint=True)
+        reps += 1
+    dt = time.perf_counter() - t0
+    gbs = reps * 2 * 2 * N * X.shape[1] * 4 / dt / 1e9
+    return {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{X.shape[1]} of {NCOLS} columns, forward + adjoint, {reps} repetitions in {dt:.1f} s"}
+
+
+def timed_loop(fn, steps, flush, stream, torch):
+    """Sum of per-step CUDA-event times; L2 flushed (outside the events) before each step."""
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        starts[i].record(stream)
+        fn()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    return [s.elapsed_time(e) for s, e in zip(starts, ends)]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--rows", type=int, default=1, help="also measure the other hot-path rows")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        reference_arm(args, world, rank)
+        return
+
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1710_09578_gb300 as fm
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    stream = torch.cuda.current_stream()
+    props = torch.cuda.get_device_properties(dev)
+    l2 = getattr(props, "L2_cache_size", 126 * 1024 * 1024)
+    flush = torch.empty(2 * l2, dtype=torch.uint8, device=dev)
+
+    xf, xi = I.hadamard_block()
+    Xh = torch.from_numpy(xf).pin_memory()
+    X = Xh.to(dev)
+    Y = torch.empty_like(X)
+    Z = torch.empty_like(X)
+    A = fm.hadamard(LOG2N)
+
+    def step():
+        A.forward(X, out=Y)
+        A.backward(Y, out=Z)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    l0 = fm.launch_count()
+    with Clocks(local) as clk:
+        times = timed_loop(step, args.steps, flush, stream, torch)
+    launches = fm.launch_count() - l0
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    t_total = sum(times) / 1e3
+    if pg:
+        tt = torch.tensor([t_total], device=dev, dtype=torch.float64)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        t_total = tt.item()
+    value = world * STEP_BYTES * args.steps / t_total / 1e9
+
+    # ---- roofline of the dominant kernel: one fwht_tile_kernel launch per apply
+    per_launch = timed_loop(lambda: A.forward(X, out=Y), 200, flush, stream, torch)
+    launch_s = float(np.mean(per_launch)) / 1e3
+    peak, peak_src = _peaks()
+    achieved = APPLY_BYTES / launch_s / 1e9
+
+    # ---- end to end through the public API with host buffers
+    out_h = torch.empty_like(Xh).pin_memory()
+    e2e_steps = max(20, args.steps // 20)
+
+    def e2e_step():
+        Xd = Xh.to(dev, non_blocking=True)
+        Yd = A.forward(Xd)
+        Zd = A.backward(Yd)
+        out_h.copy_(Zd, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    e2e_val = world * STEP_BYTES * e2e_steps / t_e2e / 1e9
+
+    rows = {}
+    if args.rows and rank == 0:
+        rows = measure_rows(fm, torch, dev, stream, flush, xi)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_total / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N, "columns": NCOLS, "bytes_per_step": STEP_BYTES,
+                       "l2": "flushed (2x L2 memset) before every timed step, outside the events",
+                       "parallelism": f"replicas x{world}"},
+            "clocks": clk.summary(),
+            "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": N * NCOLS * 4,
+                    "d2h_bytes_per_step": N * NCOLS * 4},
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": NCU_TRAFFIC, "kernel": "fwht_tile_kernel",
+                         "peak_source": peak_src, "algorithmic_bytes_per_launch": APPLY_BYTES},
+            "rows": rows,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+def _gbs_loop(fn, nbytes, steps, flush, stream, torch):
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    ts = timed_loop(fn, steps, flush, stream, torch)
+    return nbytes * steps / (sum(ts) / 1e3) / 1e9
+
+
+def measure_rows(fm, torch, dev, stream, flush, xi):
+    """GB/s of the other hot-path rows (forward + adjoint, algorithmic bytes)."""
+    rows = {}
+    # int8 -> int32 Hadamard (exact)
+    Xi = torch.from_numpy(xi).to(dev)
+    Ai = fm.hadamard(LOG2N, fm.FM_HAD_INT8)
+    Yi = torch.empty((NCOLS, N), dtype=torch.int32, device=dev)
+    rows["hadamard_int8_fwd"] = {"GB/s": _gbs_loop(lambda: Ai.forward(Xi, out=Yi), N * NCOLS * 5, 200, flush,
+                                                   stream, torch)}
+    del Xi, Yi
+    # compressed-sensing operator Phi = P Diag(d) C, N = 2^18, 64 complex64 columns
+    c, d, idx, X, Yc, _ = I.cs_operator()
+    n = len(c)
+    m = len(idx)
+    A = fm.product(fm.partial(idx, n), fm.diag(d), fm.circulant(c))
+    Xg = torch.from_numpy(X).to(dev)
+    Ygo = torch.empty((64, m), dtype=torch.complex64, device=dev)
+    Zg = torch.empty((64, n), dtype=torch.complex64, device=dev)
+    A.reserve(64, torch.complex64)
+    byts = 2 * (64 * n * 8 + 64 * m * 8 + n * 8 * 2 + m * 4)
+    rows["cs_PDC_2p18x64_fwd+adj"] = {
+        "GB/s": _gbs_loop(lambda: (A.forward(Xg, out=Ygo), A.backward(Ygo, out=Zg)), byts, 50, flush, stream,
+                          torch), "algorithmic_bytes": byts}
+    del Xg, Ygo, Zg, A
+    # Kron(H_256, C_1024, F_64), N = 2^24, 4 complex64 columns
+    ck, Xk, _ = I.kron_large()
+    K = fm.kron(fm.hadamard(8), fm.circulant(ck), fm.fourier(64))
+    Xg = torch.from_numpy(Xk).to(dev)
+    Yg = torch.empty_like(Xg)
+    Zg = torch.empty_like(Xg)
+    K.reserve(4, torch.complex64)
+    byts = 2 * 2 * Xk.nbytes
+    rows["kron_2p24x4_fwd+adj"] = {
+        "GB/s": _gbs_loop(lambda: (K.forward(Xg, out=Yg), K.backward(Yg, out=Zg)), byts, 20, flush, stream,
+                          torch), "algorithmic_bytes": byts}
+    del Xg, Yg, Zg, K
+    # complex128 circulant N = 4096, 16 columns
+    c0, X0, _ = I.circulant_tiny()
+    C0 = fm.circulant(c0)
+    X0g = torch.from_numpy(X0).to(dev)
+    Y0 = torch.empty_like(X0g)
+    Z0 = torch.empty_like(X0g)
+    byts = 2 * (2 * X0.nbytes + 4096 * 16)
+    rows["circulant_c128_4096x16_fwd+adj"] = {
+        "GB/s": _gbs_loop(lambda: (C0.forward(X0g, out=Y0), C0.backward(Y0, out=Z0)), byts, 200, flush, stream,
+                          torch), "algorithmic_bytes": byts}
+    return rows
+
+
+if __name__ == "__main__":
+    main()

@@ -34,6 +34,11 @@ struct VecInfo {
   int64_t soff;     // spectrum row offset
 };
 
+template <typename C>
+__host__ __device__ constexpr size_t fft_vinfo_offset(int E) {
+  return (((size_t)(E + E / 16 + 1) * sizeof(C)) + 15) & ~(size_t)15;
+}
+
 template <typename T>
 __device__ __forceinline__ typename Cx<T>::t fft_load(const FftArgs<T>& a, const VecInfo& vi, int t) {
   typedef typename Cx<T>::t C;
@@ -211,7 +216,8 @@ __global__ void __launch_bounds__(THREADS) fft_tile_kernel(const __grid_constant
   constexpr int E = THREADS * EPT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
-  VecInfo* vinfo = reinterpret_cast<VecInfo*>(smem_raw + (size_t)(E + E / 16 + 1) * sizeof(C));
+  // per-vector table after the padded tile, on a 16-byte boundary (it holds int64 fields)
+  VecInfo* vinfo = reinterpret_cast<VecInfo*>(smem_raw + fft_vinfo_offset<C>(E));
   const int logL = a.logL, logV = a.logV, vfast = a.vfast, V = a.V;
   const int64_t g0 = (int64_t)blockIdx.x * V;
   const int64_t nvec = a.ncu * a.outer * a.inner;
@@ -319,7 +325,7 @@ static fm_status launch_cfg(FftArgs<T> a, cudaStream_t st) {
   a.out_vcontig = (a.inner > 1 || a.out_ostride == 1) ? 1 : 0;
   // passes run with vectors fastest when a tile holds enough of them
   a.vfast = a.V >= 16 ? 1 : 0;
-  const size_t smem = (size_t)(E + E / 16 + 1) * sizeof(C) + (size_t)a.V * sizeof(VecInfo);
+  const size_t smem = fft_vinfo_offset<C>(E) + (size_t)a.V * sizeof(VecInfo);
   auto kern = fft_tile_kernel<T, THREADS, EPT>;
   int dev = 0;
   cudaGetDevice(&dev);

@@ -83,6 +83,11 @@ __device__ __forceinline__ void wht_pass(W* s, int sh, int logLp, int logV, int 
   }
 }
 
+template <typename W>
+__host__ __device__ constexpr size_t fwht_vinfo_offset(int E) {
+  return (((size_t)(E + E / 16 + 1) * sizeof(W)) + 15) & ~(size_t)15;
+}
+
 struct WVec {
   int64_t in_off;   // -1 if absent
   int64_t out_off;
@@ -93,7 +98,8 @@ __global__ void __launch_bounds__(THREADS) fwht_tile_kernel(const __grid_constan
   constexpr int E = THREADS * EPT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   W* s = reinterpret_cast<W*>(smem_raw);
-  WVec* vinfo = reinterpret_cast<WVec*>(smem_raw + (size_t)(E + E / 16 + 1) * sizeof(W));
+  // per-vector table after the padded tile, on a 16-byte boundary (it holds int64 fields)
+  WVec* vinfo = reinterpret_cast<WVec*>(smem_raw + fwht_vinfo_offset<W>(E));
   const int logLp = a.logLp, logV = a.logV, V = 1 << a.logV;
   const int C = 1 << a.logC;
   // blockIdx.x = tile * C + part
@@ -179,7 +185,7 @@ static fm_status fwht_cfg(FwhtArgs a, cudaStream_t st) {
   const int64_t tiles = (nvec + (1 << a.logV) - 1) >> a.logV;
   const int64_t blocks = tiles << a.logC;
   if (blocks > 0x7fffffffLL) { set_error("fwht: too many tiles"); return FM_ERR_UNSUPPORTED; }
-  const size_t smem = (size_t)(E + E / 16 + 1) * sizeof(W) + ((size_t)1 << a.logV) * sizeof(WVec);
+  const size_t smem = fwht_vinfo_offset<W>(E) + ((size_t)1 << a.logV) * sizeof(WVec);
   auto kern = fwht_tile_kernel<Tin, W, Tout, THREADS, EPT>;
   int dev = 0;
   cudaGetDevice(&dev);

@@ -9,8 +9,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 @pytest.fixture(scope="module")
 def L():
-    from paper_1710_09578_gb300.build import build
-    build()
+    import __graft_entry__
+    __graft_entry__.build()
     from paper_1710_09578_gb300 import _lib
     return _lib
 
