@@ -145,6 +145,30 @@ fm_status fm_backward(fm_op A, const void* Y, int64_t ldy, fm_dtype ydt, void* X
 /* Grow A's workspace for up to ncols columns of type xdt (both directions). */
 fm_status fm_reserve(fm_op A, int64_t ncols, fm_dtype xdt, void* stream);
 
+/* Circulant transform that allocates no device memory.  (The paper has no counterpart:
+ * this is a deployment aid, not part of the method.)
+ * For callers that cannot allocate device memory while they apply an operator -- a
+ * program whose device memory belongs to another allocator or to a fixed budget, or code
+ * that must avoid the implicit device synchronisation of cudaMalloc / cudaFree.  It
+ * computes the same result as fm_forward (adjoint = 0) or fm_backward (adjoint = 1) of
+ * the Circulant operator C on ncols complex64 columns (X, Y: device buffers, leading
+ * dimensions ldx, ldy >= n; Y must not overlap X), but the scratch of the two-pass plan
+ * used for n > 16384 comes from a fixed 16 MiB array in the library's device image
+ * (reserved on every GPU that loads the library, held until exit) instead of the
+ * operator's growable workspace.  It calls no cudaMalloc, cudaFree or allocating routine.
+ * Limits and rules:
+ *   - the scratch needed is n * ncols * 8 bytes when n > 16384 (nothing below that); a
+ *     call needing more than 16 MiB returns FM_ERR_UNSUPPORTED: split the columns;
+ *   - C must come from fm_circulant on the current device (FM_ERR_INVALID_ARG otherwise);
+ *   - the first call on a device looks up the array's device address (set-up); make that
+ *     first call before capturing any stream;
+ *   - all calls share the one array, which keeps what the last call wrote (every element
+ *     a call reads it has written first, so nothing needs clearing): calls that overlap
+ *     on the GPU -- on different streams, or from different threads -- race, so serialise
+ *     them (one stream). */
+fm_status fm_circulant_apply_noalloc(fm_op C, int adjoint, const void* X, int64_t ldx, void* Y, int64_t ldy,
+                                     int64_t ncols, void* stream);
+
 /* ---------------------------------------------------------------- FISTA */
 
 /* Batched FISTA (accelerated proximal gradient, cited in Sec. 3) for

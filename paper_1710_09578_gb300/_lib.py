@@ -65,6 +65,7 @@ _SIGS = {
     "fm_forward": [_op, _p, _i64, _i32, _p, _i64, _i32, _i64, _p],
     "fm_backward": [_op, _p, _i64, _i32, _p, _i64, _i32, _i64, _p],
     "fm_reserve": [_op, _i64, _i32, _p],
+    "fm_circulant_apply_noalloc": [_op, _i32, _p, _i64, _p, _i64, _i64, _p],
     "fm_batch_create": [_opp, _i64, _p, _opp],
     "fm_batch_sizes": [_p, ctypes.POINTER(_i64), ctypes.POINTER(_i64)],
     "fm_fista": [_p, _p, _p, ctypes.POINTER(fm_fista_params), ctypes.POINTER(fm_fista_report), _p],
@@ -177,6 +178,12 @@ def fm_backward(h, Y: int, ldy: int, ydt: int, X: int, ldx: int, xdt: int, ncols
 
 def fm_reserve(h, ncols: int, xdt: int, stream: int = 0):
     check(lib.fm_reserve(h, ncols, xdt, stream), "fm_reserve")
+
+
+def fm_circulant_apply_noalloc(h, adjoint: int, X: int, ldx: int, Y: int, ldy: int, ncols: int,
+                               stream: int = 0):
+    check(lib.fm_circulant_apply_noalloc(h, adjoint, X, ldx, Y, ldy, ncols, stream),
+          "fm_circulant_apply_noalloc")
 
 
 def fm_batch_create(handles, stream: int = 0):

@@ -45,6 +45,12 @@ fm_status device_tables(int device, DeviceTables** out) {
   return FM_OK;
 }
 
+DeviceTables* device_tables_if_ready(int device) {
+  if (device < 0 || device >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(g_tab_mu);
+  return g_tab_ready[device] ? &g_tabs[device] : nullptr;
+}
+
 void op_retain(fm_op_s* A) { A->refs.fetch_add(1); }
 
 static void free_op(fm_op_s* A) {

@@ -76,6 +76,8 @@ struct DeviceTables {
   double2* tw64 = nullptr;
 };
 fm_status device_tables(int device, DeviceTables** out);
+// The tables of `device` if they exist already, else nullptr (never allocates).
+DeviceTables* device_tables_if_ready(int device);
 
 // ------------------------------------------------------------------ operators
 enum OpKind {
