@@ -504,7 +504,6 @@ static fm_status exec_hadamard(const fm_op_s* A, const View& in, const View& out
     }
     return exec_pointwise(A, false, in, out, ncols, beta, ctx);
   }
-  if (ctx.dry) return FM_OK;
   FwhtArgs a;
   a.logL = A->log2n;
   a.ncols = ncols;
@@ -519,6 +518,7 @@ static fm_status exec_hadamard(const fm_op_s* A, const View& in, const View& out
   a.out_ostride = out.ostride;
   a.out_tstride = out.inner;
   a.beta = beta;
+  if (ctx.dry) return FM_OK;
   if (A->had_mode == FM_HAD_BF16 || A->had_mode == FM_HAD_BF16X2)
     return fwht_mma_launch(a, A->had_mode == FM_HAD_BF16X2 ? 1 : 0, ctx.st);
   return fwht_launch(a, in.dt, ctx.st);

@@ -171,6 +171,142 @@ __global__ void __launch_bounds__(THREADS) fwht_tile_kernel(const __grid_constan
   }
 }
 
+// ------------------------------------------------------------------ long contiguous columns
+// n = C * 2^14 with plain column blocks (f32 or int8 -> int32).  CTA r of a column owns
+// block r (2^14 elements, 64 KB of FP32/int32 in shared memory) and 512 threads with 32
+// elements each.  Element e of the block has bits 0..13; the transform is done in three
+// register rounds over bit groups {0,1,11,12,13}, {2..6} and {7..10} with two shared-memory
+// exchanges in between; the first round loads straight from HBM (16-byte vectors, all the
+// C blocks combined with row r of H_C as they arrive) and the last round stores straight
+// to HBM (each warp writes 128 contiguous bytes per instruction).
+// Shared-memory word of element e: e ^ (((e >> 7) & 31) << 2), which keeps 16-byte groups
+// intact and makes every access pattern below bank-conflict free.
+__device__ __forceinline__ int lswz(int e) { return e ^ (((e >> 7) & 31) << 2); }
+
+template <typename W> struct Vec4;
+template <> struct Vec4<float> { typedef float4 t; };
+template <> struct Vec4<int> { typedef int4 t; };
+
+__device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ int4 ld4(const int* p) { return __ldg(reinterpret_cast<const int4*>(p)); }
+__device__ __forceinline__ int4 ld4(const int8_t* p) {
+  const char4 c = __ldg(reinterpret_cast<const char4*>(p));
+  return make_int4(c.x, c.y, c.z, c.w);
+}
+__device__ __forceinline__ float4 make_vec4(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
+__device__ __forceinline__ int4 make_vec4(int a, int b, int c, int d) { return make_int4(a, b, c, d); }
+
+template <typename V> __device__ __forceinline__ void acc4(V& a, const V& b, bool neg) {
+  if (neg) { a.x -= b.x; a.y -= b.y; a.z -= b.z; a.w -= b.w; }
+  else { a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w; }
+}
+
+template <typename Tin, typename W, int C>
+__global__ void __launch_bounds__(512, 2) fwht_long_kernel(const Tin* __restrict__ in, int64_t in_ld,
+                                                           W* __restrict__ out, int64_t out_ld, int beta,
+                                                           int nparts) {
+  typedef typename Vec4<W>::t V4;
+  constexpr int LP = 1 << 14;
+  __shared__ __align__(16) W s[LP];
+  // C > 1: CTA `part` combines the C blocks of its column with row `part` of H_C.
+  // C == 1: CTA `part` transforms block `part` of nparts on its own.
+  const int np = C > 1 ? C : nparts;
+  const int part = (int)(blockIdx.x % np);
+  const int64_t col = blockIdx.x / np;
+  const int t = threadIdx.x;
+  const Tin* x = in + col * in_ld + (C > 1 ? 0 : (int64_t)part * LP);
+  W r[32];
+
+  // round A: e = c + 4 t + 2048 q, registers hold bits {0,1} (c) and {11,12,13} (q)
+  {
+    V4 acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = ld4(x + 4 * t + 2048 * q);
+#pragma unroll
+    for (int sb = 1; sb < C; ++sb) {
+      const bool neg = __popc(sb & part) & 1;
+#pragma unroll
+      for (int hq = 0; hq < 8; hq += 4) {
+        V4 v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = ld4(x + (int64_t)sb * LP + 4 * t + 2048 * (hq + q));
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc4(acc[hq + q], v[q], neg);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      r[4 * q + 0] = acc[q].x;
+      r[4 * q + 1] = acc[q].y;
+      r[4 * q + 2] = acc[q].z;
+      r[4 * q + 3] = acc[q].w;
+    }
+  }
+  wht_regs<W, 32>(r);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int e = 4 * t + 2048 * q;
+    *reinterpret_cast<V4*>(&s[lswz(e)]) = make_vec4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+  }
+  __syncthreads();
+
+  // round B: e = a + 4 k + 128 b with a = t & 3, b = t >> 2; registers hold bits 2..6 (k)
+  {
+    const int base = (t & 3) + 128 * (t >> 2);
+#pragma unroll
+    for (int k = 0; k < 32; ++k) r[k] = s[lswz(base + 4 * k)];
+    wht_regs<W, 32>(r);
+#pragma unroll
+    for (int k = 0; k < 32; ++k) s[lswz(base + 4 * k)] = r[k];
+  }
+  __syncthreads();
+
+  // round C: e = l + 128 m + 2048 h with l = t & 127, h = 2 (t >> 7) + g; registers hold
+  // bits 7..10 (m) for g = 0, 1
+  {
+    const int l = t & 127, h0 = 2 * (t >> 7);
+#pragma unroll
+    for (int g = 0; g < 2; ++g)
+#pragma unroll
+      for (int m = 0; m < 16; ++m) r[16 * g + m] = s[lswz(l + 128 * m + 2048 * (h0 + g))];
+    wht_regs<W, 16>(r);
+    wht_regs<W, 16>(r + 16);
+    W* y = out + col * out_ld + (int64_t)part * LP;
+#pragma unroll
+    for (int g = 0; g < 2; ++g)
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        W* p = y + l + 128 * m + 2048 * (h0 + g);
+        *p = beta ? *p + r[16 * g + m] : r[16 * g + m];
+      }
+  }
+}
+
+template <typename Tin, typename W>
+static fm_status fwht_long(const FwhtArgs& a, cudaStream_t st) {
+  const int logC = a.logL - 14;
+  const Tin* in = reinterpret_cast<const Tin*>(a.in);
+  W* out = reinterpret_cast<W*>(a.out);
+  if (a.ncols == 0) return FM_OK;
+  const int64_t blocks = a.ncols << logC;
+  switch (logC) {
+    case 0: fwht_long_kernel<Tin, W, 1><<<(unsigned)blocks, 512, 0, st>>>(in, a.in_ld, out, a.out_ld, a.beta, 1); break;
+    case 1: fwht_long_kernel<Tin, W, 2><<<(unsigned)blocks, 512, 0, st>>>(in, a.in_ld, out, a.out_ld, a.beta, 2); break;
+    case 2: fwht_long_kernel<Tin, W, 4><<<(unsigned)blocks, 512, 0, st>>>(in, a.in_ld, out, a.out_ld, a.beta, 4); break;
+    default: set_error("fwht_long: unsupported length"); return FM_ERR_UNSUPPORTED;
+  }
+  return after_launch("fwht_long_kernel");
+}
+
+// Plain contiguous column blocks of length 2^14..2^16 with 16-byte aligned columns.
+static bool long_path_ok(const FwhtArgs& a, int in_size) {
+  if (a.logL < 14 || a.logL > 16 || a.outer != 1 || a.inner != 1) return false;
+  if (a.in_tstride != 1 || a.out_tstride != 1) return false;
+  if (((uintptr_t)a.in % (4 * in_size)) || ((uintptr_t)a.out % 16)) return false;
+  if ((a.in_ld * in_size) % (4 * in_size) || (a.out_ld * 4) % 16) return false;
+  return true;
+}
+
 template <typename Tin, typename W, typename Tout, int THREADS, int EPT>
 static fm_status fwht_cfg(FwhtArgs a, cudaStream_t st) {
   constexpr int E = THREADS * EPT;
@@ -202,6 +338,8 @@ static fm_status fwht_cfg(FwhtArgs a, cudaStream_t st) {
 
 fm_status fwht_launch(FwhtArgs a, fm_dtype in_dt, cudaStream_t st) {
   if (a.logL < 1) { set_error("fwht: n must be >= 2"); return FM_ERR_UNSUPPORTED; }
+  if (in_dt == FM_F32 && long_path_ok(a, 4)) return fwht_long<float, float>(a, st);
+  if (in_dt == FM_I8 && long_path_ok(a, 1)) return fwht_long<int8_t, int>(a, st);
   switch (in_dt) {
     case FM_F32: return fwht_cfg<float, float, float, 512, 32>(a, st);
     case FM_C64: return fwht_cfg<float2, float2, float2, 512, 16>(a, st);

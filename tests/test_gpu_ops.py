@@ -157,6 +157,27 @@ def test_hadamard_int8_exact(fm, log2n):
     assert np.array_equal(got_b.astype(np.int64), want)
 
 
+@pytest.mark.parametrize("log2n", [4, 5, 7, 10, 13, 14, 15, 16])
+@pytest.mark.parametrize("mode,tol", [("FM_HAD_BF16", 2e-2), ("FM_HAD_BF16X2", 1e-5)])
+def test_hadamard_bf16_tensor_cores(fm, log2n, mode, tol):
+    n = 1 << log2n
+    A = fm.hadamard(log2n, getattr(fm, mode))
+    X = blk(3, n, np.float32)
+    got = A.forward(gpu(X)).cpu().numpy()
+    want = O.Hadamard(n).apply(X.T.astype(np.float64)).T
+    assert colerr(got, want) <= tol
+    got_b = A.backward(gpu(X)).cpu().numpy()
+    assert colerr(got_b, want) <= tol
+
+
+def test_hadamard_bf16_workload_full(fm):
+    xf, _ = I.hadamard_block()
+    want = O.Hadamard(1 << 16).apply(xf.T.astype(np.float64)).T
+    for mode, tol in (("FM_HAD_BF16", 2e-2), ("FM_HAD_BF16X2", 1e-5)):
+        got = fm.hadamard(16, getattr(fm, mode)).forward(gpu(xf)).cpu().numpy()
+        assert colerr(got, want) <= tol, mode
+
+
 def test_hadamard_workload_full(fm):
     # the 2^16 x 256 block: FP32 within tolerance, int8 bit-exact
     xf, xi = I.hadamard_block()
