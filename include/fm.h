@@ -203,7 +203,7 @@ typedef struct {
 } fm_fista_report;
 
 /* A batch of `count` instances, each A_i = Product(Partial(idx_i, n_i), Toeplitz(t_i))
- * with real t_i (n_i x n_i, n_i a power of two in [2^4, 2^14]) and m_i selected rows;
+ * with real t_i (n_i x n_i, n_i a power of two in [2^8, 2^14]) and m_i selected rows;
  * other operator shapes give FM_ERR_UNSUPPORTED.  Building the batch uploads a
  * work list (instances sorted by size) and allocates the per-instance state. */
 fm_status fm_batch_create(const fm_op* A, int64_t count, void* stream, fm_batch* out);

@@ -1,19 +1,605 @@
-// Batched FISTA (placeholder until the persistent kernel lands).
-#include "fm_internal.h"
+// Batched FISTA for l1-regularised least squares, min 1/2 ||A x - b||^2 + lambda ||x||_1
+// (Eq. (8) with tau = 2 lambda), with A_i = P_i T_i (row selection of a real Toeplitz matrix)
+// for thousands of independent instances in ONE persistent launch.
+//
+// The recovery loop of the paper (Sec. 3: ISTA, and the accelerated variant it uses for its
+// reconstructions) spends its time in phi_A and beta_A; here both run in shared memory:
+// T y is the non-circular convolution of y with t, evaluated through the circulant
+// embedding of length L = 2n (Sec. 2.1.1).  y is real, so the length-L transform is done
+// as one complex FFT of length n on z[k] = w[2k] + i w[2k+1] (w = [y; 0]): a post-step
+// turns Z = FFT_n(z) into the half spectrum W[k] = E[k] + exp(-2 pi i k / L) O[k]
+// (E, O the spectra of the even and odd samples), multiplies by the embedding spectrum,
+// and a pre-step folds the product back into the spectrum of [v_even + i v_odd] for the
+// inverse FFT of length n.  Each product with T or T^T therefore costs two complex FFTs of
+// length n on a 2^14-element tile, i.e. up to 128 KB of shared memory per CTA.
+//
+// Work list: instances sorted by size, grouped so that a group of V = 2^14 / n instances of
+// the same n fills one tile and runs in lock step (the FISTA momentum sequence t_k does not
+// depend on the data, only L and lambda are per instance).  Each CTA takes the next group
+// with an atomic counter (no waiting on other CTAs) and keeps it until all its steps are
+// done: lambda = lambda_rel ||A^T b||_inf, L = min(safety ||A v_P||^2, max|c_hat|^2) after P
+// power iterations from v_0 = ones / sqrt(n), K FISTA steps from x_0 = y_1 = 0, t_1 = 1, and
+// the final objective.  x_k lives in the caller's x buffer, y_k in the batch's scratch
+// (both small enough to stay in L2 while a group runs); norms, the Rayleigh quotient and the
+// objective are accumulated in FP64, everything else is FP32.
+#include <algorithm>
+#include <vector>
 
-struct fm_batch_s {
-  int dummy;
+#include "exec.h"
+#include "fft_impl.cuh"
+#include "pointwise.h"
+
+namespace fm {
+
+struct FInst {
+  const float2* spec;   // FFT_L(c) / L of the circulant embedding (L = 2n entries)
+  const int32_t* idx;   // m selected rows
+  int64_t b_off;        // offset of b_i in the packed b
+  int64_t x_off;        // offset of x_i in the packed x (and of y_i in the scratch)
+  int n, m, logn, pad;
+  double cap;           // max_k |FFT_L(c)_k|^2
 };
 
+struct FGroup {
+  int logn, count, first, pad;
+};
+
+struct FistaArgs {
+  const FInst* inst;
+  const int32_t* order;    // instance indices sorted by group
+  const FGroup* groups;
+  int ngroups;
+  int single_group;        // >= 0: only this group (one launch per instance)
+  const float* b;
+  float* x;
+  float* y;
+  const float2* tw;        // W_{2^14}^m, FFT passes
+  const float2* tw2;       // W_{2^15}^m, real-FFT pre/post steps
+  int iters, power_iters;
+  double lambda_rel, safety;
+  int accel;
+  double* rep_L;
+  double* rep_lambda;
+  double* rep_obj;
+  int32_t* rep_status;
+  int* counter;
+};
+
+constexpr int kFThreads = 512, kFEpt = 32, kFE = kFThreads * kFEpt;  // 2^14 complex per tile
+constexpr int kFMaxV = 64;                                               // n >= 256
+
+struct VState {
+  const float2* spec;
+  const int32_t* idx;
+  int64_t b_off, x_off;
+  int m, valid, inst, pad;
+  float invL, thr;
+  double cap, lam, L, acc;
+  unsigned amax;
+};
+
+__device__ __forceinline__ float2* zaddr(float2* s, int t, int v, int logL, int logV, int vfast) {
+  return &s[spad(lin_index(t, v, logL, logV, vfast))];
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Add val into red[v]; one atomic per warp when the whole warp works on the same vector.
+__device__ __forceinline__ void vec_add(VState* vs, int v, double val) {
+  const int v0 = __shfl_sync(0xffffffffu, v, 0);
+  if (__all_sync(0xffffffffu, v == v0)) {
+    val = warp_sum(val);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&vs[v0].acc, val);
+  } else {
+    atomicAdd(&vs[v].acc, val);
+  }
+}
+
+__device__ __forceinline__ void vec_max(VState* vs, int v, float val) {
+  atomicMax(&vs[v].amax, __float_as_uint(fabsf(val)));
+}
+
+// Natural-order FFT of every vector of the tile, in place in shared memory.
+__device__ __noinline__ void tile_fft(float2* s, int logL, int logV, int vfast, int dir, const float2* tw) {
+  int rad[6], nrad = 0, rem = logL;
+  while (rem >= 3) { rad[nrad++] = 8; rem -= 3; }
+  if (rem == 2) rad[nrad++] = 4;
+  if (rem == 1) rad[nrad++] = 2;
+  float2 r[kFEpt];
+  int logNs = 0;
+  for (int p = 0; p < nrad; ++p) {
+    const int R = rad[p];
+#define FLS(RR) regs_from_smem<RR, kFThreads, kFEpt, float2>(r, s, logL, logV, vfast)
+    FM_RADIX_SWITCH(R, FLS)
+#undef FLS
+    __syncthreads();
+#define FPC(RR) pass_compute<RR, kFThreads, kFEpt, float2>(r, logL, logV, vfast, logNs, dir, tw)
+    FM_RADIX_SWITCH(R, FPC)
+#undef FPC
+#define FPS(RR) regs_to_smem<RR, kFThreads, kFEpt, float2>(r, s, logL, logV, vfast, logNs)
+    FM_RADIX_SWITCH(R, FPS)
+#undef FPS
+    __syncthreads();
+    logNs += R == 8 ? 3 : (R == 4 ? 2 : 1);
+  }
+}
+
+// Z <- pre-step( spectrum x post-step(Z) ) for every vector: see the file comment.
+__device__ void tile_spectral(float2* s, VState* vs, int logL, int logV, int vfast, int adjoint,
+                              const float2* tw2) {
+  const int Nc = 1 << logL, half = Nc >> 1, V = 1 << logV;
+  const int tsh = 14 - logL;  // index scale into the W_{2^15} table for exp(-2 pi i k / (2 Nc))
+  for (int q = threadIdx.x; q < V * half; q += kFThreads) {
+    const int v = q >> (logL - 1), k = q & (half - 1);
+    if (!vs[v].valid) continue;
+    const int kp = Nc - k;
+    float2* pk = zaddr(s, k, v, logL, logV, vfast);
+    float2* pm = zaddr(s, kp & (Nc - 1), v, logL, logV, vfast);
+    const float2 Zk = *pk, Zm = *pm;
+    // E = (Zk + conj Zm)/2, O = (Zk - conj Zm)/(2i)
+    const float2 E = make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y));
+    const float2 O = make_float2(0.5f * (Zk.y + Zm.y), -0.5f * (Zk.x - Zm.x));
+    const float2 wk = tw2[k << tsh], wkp = tw2[kp << tsh];
+    const float2 Wk = cadd(E, cmul(wk, O));
+    const float2 Wkp = cadd(cconj(E), cmul(wkp, cconj(O)));
+    float2 sk = vs[v].spec[k], skp = vs[v].spec[kp];
+    if (adjoint) { sk = cconj(sk); skp = cconj(skp); }
+    const float2 Vk = cscale(cmul(sk, Wk), 2.f), Vkp = cscale(cmul(skp, Wkp), 2.f);
+    // Z'[k] = (V_k + conj V_kp)/2 + i exp(+2 pi i k / L) (V_k - conj V_kp)/2
+    const float2 A1 = cscale(cadd(Vk, cconj(Vkp)), 0.5f), B1 = cscale(csub(Vk, cconj(Vkp)), 0.5f);
+    *pk = cadd(A1, cmul_i(cmul(cconj(wk), B1), +1));
+    if (k > 0) {
+      const float2 A2 = cscale(cadd(Vkp, cconj(Vk)), 0.5f), B2 = cscale(csub(Vkp, cconj(Vk)), 0.5f);
+      *pm = cadd(A2, cmul_i(cmul(cconj(wkp), B2), +1));
+    }
+  }
+  // k = Nc / 2 pairs with itself: Z' = conj(c') Z with c' = 2 spec (conjugated for T^T)
+  for (int v = threadIdx.x; v < V; v += kFThreads) {
+    if (!vs[v].valid) continue;
+    float2* p = zaddr(s, half, v, logL, logV, vfast);
+    float2 c = cscale(vs[v].spec[half], 2.f);
+    if (adjoint) c = cconj(c);
+    *p = cmul(cconj(c), *p);
+  }
+}
+
+__device__ __forceinline__ float unpack(const float2* s, int m, int v, int logL, int logV, int vfast) {
+  const float2 z = s[spad(lin_index(m >> 1, v, logL, logV, vfast))];
+  return (m & 1) ? z.y : z.x;
+}
+
+// Z <- pack([w; 0]) where w is the length-n real vector at src + x_off of each vector
+__device__ void pack_from(float2* s, VState* vs, const float* src, int logL, int logV, int vfast) {
+  const int Nc = 1 << logL, V = 1 << logV;
+  for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
+    const int v = q >> logL, k = q & (Nc - 1);
+    float2 z = make_float2(0.f, 0.f);
+    if (vs[v].valid && k < (Nc >> 1)) {
+      const float* w = src + vs[v].x_off;
+      z = make_float2(w[2 * k], w[2 * k + 1]);
+    }
+    *zaddr(s, k, v, logL, logV, vfast) = z;
+  }
+}
+
+// phi: tile holds T w after the call (unpacked on demand); returns nothing
+__device__ void apply_T(float2* s, VState* vs, int logL, int logV, int vfast, int adjoint, const float2* tw,
+                        const float2* tw2) {
+  __syncthreads();
+  tile_fft(s, logL, logV, vfast, -1, tw);
+  tile_spectral(s, vs, logL, logV, vfast, adjoint, tw2);
+  __syncthreads();
+  tile_fft(s, logL, logV, vfast, +1, tw);
+}
+
+template <bool FISTA_RESID>
+__device__ void gather_rows(float (&rr)[kFEpt], const float2* s, VState* vs, const float* b, int logL, int logV,
+                            int vfast, bool sumsq) {
+  const int Nc = 1 << logL, V = 1 << logV;
+#pragma unroll
+  for (int i = 0; i < kFEpt; ++i) {
+    const int q = threadIdx.x + i * kFThreads;
+    const int v = q >> logL, j = q & (Nc - 1);
+    float r = 0.f;
+    if (q < V * Nc && vs[v].valid && j < vs[v].m) {
+      r = unpack(s, vs[v].idx[j], v, logL, logV, vfast);
+      if (FISTA_RESID) r -= b[vs[v].b_off + j];
+    }
+    rr[i] = r;
+    if (sumsq) vec_add(vs, v, (double)r * (double)r);
+  }
+}
+
+__device__ void scatter_rows(float2* s, const float (&rr)[kFEpt], VState* vs, int logL, int logV, int vfast) {
+  const int Nc = 1 << logL, V = 1 << logV;
+  __syncthreads();
+  for (int q = threadIdx.x; q < V * Nc; q += kFThreads) *zaddr(s, q & (Nc - 1), q >> logL, logL, logV, vfast) =
+      make_float2(0.f, 0.f);
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < kFEpt; ++i) {
+    const int q = threadIdx.x + i * kFThreads;
+    const int v = q >> logL, j = q & (Nc - 1);
+    if (q < V * Nc && vs[v].valid && j < vs[v].m) {
+      const int pos = vs[v].idx[j];
+      float* f = reinterpret_cast<float*>(zaddr(s, pos >> 1, v, logL, logV, vfast));
+      f[pos & 1] = rr[i];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kFThreads, 1) fista_kernel(const __grid_constant__ FistaArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* s = reinterpret_cast<float2*>(smem_raw);
+  VState* vs = reinterpret_cast<VState*>(smem_raw + fft_vinfo_offset<float2>(kFE));
+  __shared__ int s_group;
+  __shared__ double s_t;
+  bool first = true;
+  while (true) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (a.single_group >= 0) s_group = first ? a.single_group : -1;
+      else s_group = atomicAdd(a.counter, 1);
+    }
+    __syncthreads();
+    const int gi = s_group;
+    first = false;
+    if (gi < 0 || gi >= a.ngroups) break;
+    const FGroup G = a.groups[gi];
+    const int logL = G.logn, Nc = 1 << logL;
+    const int logV = 14 - logL, V = 1 << logV;
+    const int vfast = V >= 16 ? 1 : 0;
+    for (int v = threadIdx.x; v < V; v += kFThreads) {
+      VState w = {};
+      w.valid = v < G.count;
+      if (w.valid) {
+        const int ii = a.order[G.first + v];
+        const FInst in = a.inst[ii];
+        w.spec = in.spec;
+        w.idx = in.idx;
+        w.b_off = in.b_off;
+        w.x_off = in.x_off;
+        w.m = in.m;
+        w.cap = in.cap;
+        w.inst = ii;
+      }
+      vs[v] = w;
+    }
+    __syncthreads();
+    float rr[kFEpt];
+
+    // ---- lambda = lambda_rel * ||A^T b||_inf
+    for (int i = 0; i < kFEpt; ++i) {
+      const int q = threadIdx.x + i * kFThreads;
+      const int v = q >> logL, j = q & (Nc - 1);
+      rr[i] = (vs[v].valid && j < vs[v].m) ? a.b[vs[v].b_off + j] : 0.f;
+    }
+    scatter_rows(s, rr, vs, logL, logV, vfast);
+    apply_T(s, vs, logL, logV, vfast, 1, a.tw, a.tw2);
+    __syncthreads();
+    for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
+      const int v = q >> logL;
+      if (vs[v].valid) vec_max(vs, v, unpack(s, q & (Nc - 1), v, logL, logV, vfast));
+    }
+    __syncthreads();
+    for (int v = threadIdx.x; v < V; v += kFThreads) vs[v].lam = a.lambda_rel * (double)__uint_as_float(vs[v].amax);
+
+    // ---- power iteration on A^T A from ones / sqrt(n), the iterate kept in y
+    {
+      const float v0 = rsqrtf((float)Nc);
+      for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
+        const int v = q >> logL;
+        if (vs[v].valid) a.y[vs[v].x_off + (q & (Nc - 1))] = v0;
+      }
+    }
+    for (int it = 0; it < a.power_iters; ++it) {
+      __syncthreads();
+      pack_from(s, vs, a.y, logL, logV, vfast);
+      apply_T(s, vs, logL, logV, vfast, 0, a.tw, a.tw2);
+      __syncthreads();
+      gather_rows<false>(rr, s, vs, a.b, logL, logV, vfast, false);
+      scatter_rows(s, rr, vs, logL, logV, vfast);
+      apply_T(s, vs, logL, logV, vfast, 1, a.tw, a.tw2);
+      for (int v = threadIdx.x; v < V; v += kFThreads) vs[v].acc = 0.0;
+      __syncthreads();
+      for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
+        const int v = q >> logL;
+        const float w = unpack(s, q & (Nc - 1), v, logL, logV, vfast);
+        vec_add(vs, v, (double)w * (double)w);
+      }
+      __syncthreads();
+      for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
+        const int v = q >> logL;
+        if (vs[v].valid) {
+          const double nrm = sqrt(vs[v].acc);
+          const float w = unpack(s, q & (Nc - 1), v, logL, logV, vfast);
+          a.y[vs[v].x_off + (q & (Nc - 1))] = nrm > 0.0 ? (float)((double)w / nrm) : 0.f;
+        }
+      }
+    }
+    // lam_hat = ||A v||^2, L = min(safety * lam_hat, cap)
+    __syncthreads();
+    for (int v = threadIdx.x; v < V; v += kFThreads) vs[v].acc = 0.0;
+    pack_from(s, vs, a.y, logL, logV, vfast);
+    apply_T(s, vs, logL, logV, vfast, 0, a.tw, a.tw2);
+    __syncthreads();
+    gather_rows<false>(rr, s, vs, a.b, logL, logV, vfast, true);
+    __syncthreads();
+    for (int v = threadIdx.x; v < V; v += kFThreads) {
+      double L = a.safety * vs[v].acc;
+      if (vs[v].cap < L) L = vs[v].cap;
+      vs[v].L = L;
+      vs[v].invL = L > 0.0 ? (float)(1.0 / L) : 0.f;
+      vs[v].thr = L > 0.0 ? (float)(vs[v].lam / L) : 0.f;
+    }
+    // ---- FISTA from x_0 = y_1 = 0, t_1 = 1
+    for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
+      const int v = q >> logL;
+      if (vs[v].valid) {
+        a.x[vs[v].x_off + (q & (Nc - 1))] = 0.f;
+        a.y[vs[v].x_off + (q & (Nc - 1))] = 0.f;
+      }
+    }
+    if (threadIdx.x == 0) s_t = 1.0;
+    for (int k = 0; k < a.iters; ++k) {
+      __syncthreads();
+      const double t = s_t;
+      const double tn = a.accel ? 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t)) : 1.0;
+      const float beta = a.accel ? (float)((t - 1.0) / tn) : 0.f;
+      pack_from(s, vs, a.y, logL, logV, vfast);
+      apply_T(s, vs, logL, logV, vfast, 0, a.tw, a.tw2);
+      __syncthreads();
+      gather_rows<true>(rr, s, vs, a.b, logL, logV, vfast, false);
+      scatter_rows(s, rr, vs, logL, logV, vfast);
+      apply_T(s, vs, logL, logV, vfast, 1, a.tw, a.tw2);
+      __syncthreads();
+      for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
+        const int v = q >> logL;
+        if (!vs[v].valid) continue;
+        const int64_t o = vs[v].x_off + (q & (Nc - 1));
+        const float g = unpack(s, q & (Nc - 1), v, logL, logV, vfast);
+        const float yv = a.y[o], xv = a.x[o];
+        const float z = yv - g * vs[v].invL;
+        const float mag = fabsf(z) - vs[v].thr;
+        const float xn = mag > 0.f ? copysignf(mag, z) : 0.f;
+        a.x[o] = xn;
+        a.y[o] = xn + beta * (xn - xv);
+      }
+      if (threadIdx.x == 0) s_t = tn;
+    }
+    // ---- objective 1/2 ||A x - b||^2 + lambda ||x||_1 and status
+    __syncthreads();
+    for (int v = threadIdx.x; v < V; v += kFThreads) vs[v].acc = 0.0;
+    pack_from(s, vs, a.x, logL, logV, vfast);
+    apply_T(s, vs, logL, logV, vfast, 0, a.tw, a.tw2);
+    __syncthreads();
+    gather_rows<true>(rr, s, vs, a.b, logL, logV, vfast, true);
+    __syncthreads();
+    for (int v = threadIdx.x; v < V; v += kFThreads) vs[v].cap = 0.5 * vs[v].acc;  // reuse cap: data term
+    __syncthreads();
+    for (int v = threadIdx.x; v < V; v += kFThreads) vs[v].acc = 0.0;
+    __syncthreads();
+    for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
+      const int v = q >> logL;
+      const float xv = vs[v].valid ? a.x[vs[v].x_off + (q & (Nc - 1))] : 0.f;
+      vec_add(vs, v, fabs((double)xv));
+    }
+    __syncthreads();
+    for (int v = threadIdx.x; v < V; v += kFThreads) {
+      if (!vs[v].valid) continue;
+      const int ii = vs[v].inst;
+      const double obj = vs[v].cap + vs[v].lam * vs[v].acc;
+      if (a.rep_L) a.rep_L[ii] = vs[v].L;
+      if (a.rep_lambda) a.rep_lambda[ii] = vs[v].lam;
+      if (a.rep_obj) a.rep_obj[ii] = obj;
+      if (a.rep_status) a.rep_status[ii] = isfinite(obj) ? 0 : (int)FM_ERR_NUMERIC;
+    }
+  }
+}
+
+}  // namespace fm
+
+using namespace fm;
+
+struct fm_batch_s {
+  std::vector<fm_op_s*> ops;
+  int64_t count = 0, total_rows = 0, total_cols = 0;
+  int device = 0;
+  FInst* inst = nullptr;
+  int32_t* order = nullptr;
+  FGroup* groups = nullptr;        // persistent work list
+  FGroup* single = nullptr;        // one group per instance (per-instance launches)
+  std::vector<int32_t> single_index;  // instance -> its entry in `single`
+  int ngroups = 0, nsingle = 0;
+  float* y = nullptr;
+  float2* tw2 = nullptr;
+  int* counter = nullptr;
+  int sms = 1;
+};
+
+static void batch_free(fm_batch_s* B) {
+  void* bufs[] = {B->inst, B->order, B->groups, B->single, B->y, B->tw2, B->counter};
+  for (void* p : bufs)
+    if (p) cudaFree(p);
+  for (auto* o : B->ops) op_release(o);
+  delete B;
+}
+
+static size_t fista_smem() { return fft_vinfo_offset<float2>(kFE) + sizeof(VState) * kFMaxV; }
+
 extern "C" {
-fm_status fm_batch_create(const fm_op*, int64_t, void*, fm_batch* out) {
-  if (out) *out = nullptr;
-  fm::set_error("batched FISTA is not built yet");
-  return FM_ERR_UNSUPPORTED;
+
+fm_status fm_batch_create(const fm_op* A, int64_t count, void* stream, fm_batch* out) {
+  clear_error();
+  if (!out || !A || count < 1) { set_error("need at least one operator"); return FM_ERR_INVALID_ARG; }
+  std::vector<FInst> h(count);
+  int64_t brow = 0, xcol = 0;
+  for (int64_t i = 0; i < count; ++i) {
+    const fm_op_s* op = A[i];
+    if (!op || op->kind != K_PRODUCT || op->kids.size() != 2 || op->kids[0]->kind != K_PARTIAL ||
+        op->kids[1]->kind != K_TOEPLITZ) {
+      set_error("instance %lld: expected Product(Partial, Toeplitz)", (long long)i);
+      return FM_ERR_UNSUPPORTED;
+    }
+    const fm_op_s* P = op->kids[0];
+    const fm_op_s* T = op->kids[1];
+    const int64_t n = T->cols;
+    if (!T->real || T->rows != n || P->cols != n || n < 256 || n > 16384 || (n & (n - 1)) || T->L != 2 * n) {
+      set_error("instance %lld: need a real n x n Toeplitz with n a power of two in [2^8, 2^14]", (long long)i);
+      return FM_ERR_UNSUPPORTED;
+    }
+    int logn = 0;
+    while ((1LL << logn) < n) ++logn;
+    h[i].spec = T->spec32;
+    h[i].idx = P->idx;
+    h[i].b_off = brow;
+    h[i].x_off = xcol;
+    h[i].n = (int)n;
+    h[i].m = (int)P->rows;
+    h[i].logn = logn;
+    h[i].cap = T->cap;
+    brow += P->rows;
+    xcol += n;
+  }
+  // groups of equal n, largest first
+  std::vector<int32_t> order(count);
+  for (int64_t i = 0; i < count; ++i) order[i] = (int32_t)i;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t p, int32_t q) { return h[p].logn > h[q].logn; });
+  std::vector<FGroup> groups;
+  for (int64_t i = 0; i < count;) {
+    const int logn = h[order[i]].logn;
+    const int V = 1 << (14 - logn);
+    int c = 0;
+    while (i + c < count && c < V && h[order[i + c]].logn == logn) ++c;
+    groups.push_back({logn, c, (int)i, 0});
+    i += c;
+  }
+  std::vector<FGroup> single(count);
+  std::vector<int32_t> single_index(count);
+  for (int64_t r = 0; r < count; ++r) {
+    single[r] = {h[order[r]].logn, 1, (int)r, 0};
+    single_index[order[r]] = (int32_t)r;
+  }
+  fm_batch_s* B = new (std::nothrow) fm_batch_s();
+  if (!B) return FM_ERR_OOM;
+  cudaGetDevice(&B->device);
+  for (int64_t i = 0; i < count; ++i) {
+    op_retain(A[i]);
+    B->ops.push_back(A[i]);
+  }
+  B->count = count;
+  B->total_rows = brow;
+  B->total_cols = xcol;
+  B->ngroups = (int)groups.size();
+  B->nsingle = (int)count;
+  B->single_index = single_index;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMalloc(&B->inst, sizeof(FInst) * count);
+  if (e == cudaSuccess) e = cudaMalloc(&B->order, sizeof(int32_t) * count);
+  if (e == cudaSuccess) e = cudaMalloc(&B->groups, sizeof(FGroup) * groups.size());
+  if (e == cudaSuccess) e = cudaMalloc(&B->single, sizeof(FGroup) * count);
+  if (e == cudaSuccess) e = cudaMalloc(&B->y, sizeof(float) * xcol);
+  if (e == cudaSuccess) e = cudaMalloc(&B->tw2, sizeof(float2) * 32768);
+  if (e == cudaSuccess) e = cudaMalloc(&B->counter, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(B->inst, h.data(), sizeof(FInst) * count, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(B->order, order.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(B->groups, groups.data(), sizeof(FGroup) * groups.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(B->single, single.data(), sizeof(FGroup) * count, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    set_error("batch setup: %s", cudaGetErrorString(e));
+    batch_free(B);
+    return e == cudaErrorMemoryAllocation ? FM_ERR_OOM : FM_ERR_CUDA;
+  }
+  fm_status s = twiddle_launch(32768, B->tw2, nullptr, st);
+  if (s == FM_OK) {
+    DeviceTables* t;
+    s = device_tables(B->device, &t);
+  }
+  if (s == FM_OK) {
+    e = cudaFuncSetAttribute(fista_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fista_smem());
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&B->sms, cudaDevAttrMultiProcessorCount, B->device);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      set_error("batch setup: %s", cudaGetErrorString(e));
+      s = FM_ERR_CUDA;
+    }
+  }
+  if (s != FM_OK) {
+    batch_free(B);
+    return s;
+  }
+  *out = B;
+  return FM_OK;
 }
-void fm_batch_release(fm_batch) {}
-fm_status fm_batch_sizes(fm_batch, int64_t*, int64_t*) { return FM_ERR_UNSUPPORTED; }
-fm_status fm_fista(fm_batch, const float*, float*, const fm_fista_params*, const fm_fista_report*, void*) {
-  return FM_ERR_UNSUPPORTED;
+
+void fm_batch_release(fm_batch B) {
+  if (B) batch_free(B);
 }
+
+fm_status fm_batch_sizes(fm_batch B, int64_t* rows, int64_t* cols) {
+  if (!B || !rows || !cols) { set_error("null pointer"); return FM_ERR_INVALID_ARG; }
+  *rows = B->total_rows;
+  *cols = B->total_cols;
+  return FM_OK;
 }
+
+fm_status fm_fista(fm_batch B, const float* b, float* x, const fm_fista_params* p, const fm_fista_report* rep,
+                   void* stream) {
+  clear_error();
+  if (!B || !b || !x || !p) { set_error("null pointer"); return FM_ERR_INVALID_ARG; }
+  if (p->iters < 0 || p->power_iters < 1 || !(p->safety > 0.0) || !(p->lambda_rel >= 0.0) ||
+      (p->mode != 0 && p->mode != 1)) {
+    set_error("bad FISTA parameters");
+    return FM_ERR_INVALID_ARG;
+  }
+  int dev = 0;
+  FM_CUDA(cudaGetDevice(&dev));
+  if (dev != B->device) { set_error("batch lives on device %d, current is %d", B->device, dev); return FM_ERR_INVALID_ARG; }
+  DeviceTables* tabs = device_tables_if_ready(dev);
+  if (!tabs) { set_error("device tables missing"); return FM_ERR_INVALID_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  FistaArgs a;
+  a.inst = B->inst;
+  a.order = B->order;
+  a.b = b;
+  a.x = x;
+  a.y = B->y;
+  a.tw = tabs->tw32;
+  a.tw2 = B->tw2;
+  a.iters = p->iters;
+  a.power_iters = p->power_iters;
+  a.lambda_rel = p->lambda_rel;
+  a.safety = p->safety;
+  a.accel = p->accel ? 1 : 0;
+  a.rep_L = rep ? rep->L : nullptr;
+  a.rep_lambda = rep ? rep->lambda : nullptr;
+  a.rep_obj = rep ? rep->objective : nullptr;
+  a.rep_status = rep ? rep->status : nullptr;
+  a.counter = B->counter;
+  const size_t smem = fista_smem();
+  if (p->mode == 0) {
+    a.groups = B->groups;
+    a.ngroups = B->ngroups;
+    a.single_group = -1;
+    FM_CUDA(cudaMemsetAsync(B->counter, 0, sizeof(int), st));
+    const int grid = std::min(B->ngroups, B->sms);
+    fista_kernel<<<grid, kFThreads, smem, st>>>(a);
+    return after_launch("fista_kernel");
+  }
+  // one instance per launch, in the caller's order
+  a.groups = B->single;
+  a.ngroups = B->nsingle;
+  for (int64_t i = 0; i < B->count; ++i) {
+    a.single_group = B->single_index[i];
+    fista_kernel<<<1, kFThreads, smem, st>>>(a);
+    FM_TRY(after_launch("fista_kernel"));
+  }
+  return FM_OK;
+}
+
+}  // extern "C"
