@@ -37,9 +37,9 @@ APPLY_BYTES = 2 * N * NCOLS * 4            # read X + write Y, FP32
 STEP_BYTES = 2 * APPLY_BYTES               # forward + adjoint
 METRIC = "fwd+adjoint apply GB/s vs HBM peak; batched FISTA solves/s at 1e-4 rel err"
 WORKLOAD = "Sylvester Hadamard n=2^16, 256 FP32 columns, forward + adjoint"
-# DRAM bytes of one fwht_tile_kernel launch on this workload, from the ncu capture
-# summarised in profiles/fwht_tile_kernel_hadamard_2p16x256.md (None until captured).
-NCU_TRAFFIC = None
+# DRAM bytes of one fwht_long_kernel launch on this workload, from the ncu capture
+# summarised in profiles/fwht_long_kernel_hadamard_2p16x256.md (read 67.14 MB + write 23.23 MB).
+NCU_TRAFFIC = 90361856
 
 
 def _peaks():
@@ -177,6 +177,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--rows", type=int, default=1, help="also measure the other hot-path rows")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", default=None, choices=["hadamard", "hadamard_int8", "hadamard_bf16", "cs", "kron",
+                                                        "circulant_c128", "fista"],
+                    help="run one workload a few times and exit (for ncu captures)")
     args = ap.parse_args()
     world, rank, local = dist_init()
     if args.impl == "reference":
@@ -190,6 +193,9 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.profile:
+        profile_run(fm, torch, dev, args.profile, args.steps)
+        return
     pg = None
     if world > 1:
         import torch.distributed as dist
@@ -259,7 +265,7 @@ def main():
 
     rows = {}
     if args.rows and rank == 0:
-        rows = measure_rows(fm, torch, dev, stream, flush, xi)
+        rows = measure_rows(fm, torch, dev, stream, flush, xi, cpu_sample=not args.no_cpu_baseline)
 
     if rank == 0:
         line = {
@@ -274,7 +280,7 @@ def main():
                     "d2h_bytes_per_step": N * NCOLS * 4},
             "gpu_launches": int(launches),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": NCU_TRAFFIC, "kernel": "fwht_tile_kernel",
+                         "frac": achieved / peak, "traffic": NCU_TRAFFIC, "kernel": "fwht_long_kernel",
                          "peak_source": peak_src, "algorithmic_bytes_per_launch": APPLY_BYTES},
             "rows": rows,
         }
@@ -293,7 +299,7 @@ def _gbs_loop(fn, nbytes, steps, flush, stream, torch):
     return nbytes * steps / (sum(ts) / 1e3) / 1e9
 
 
-def measure_rows(fm, torch, dev, stream, flush, xi):
+def measure_rows(fm, torch, dev, stream, flush, xi, cpu_sample=True):
     """GB/s of the other hot-path rows (forward + adjoint, algorithmic bytes)."""
     rows = {}
     # int8 -> int32 Hadamard (exact)
@@ -339,7 +345,99 @@ def measure_rows(fm, torch, dev, stream, flush, xi):
     rows["circulant_c128_4096x16_fwd+adj"] = {
         "GB/s": _gbs_loop(lambda: (C0.forward(X0g, out=Y0), C0.backward(Y0, out=Z0)), byts, 200, flush, stream,
                           torch), "algorithmic_bytes": byts}
+    rows["fista_4096"] = measure_fista(fm, torch, dev, stream, cpu_sample)
     return rows
+
+
+FISTA_INSTANCES = 4096
+
+
+def profile_run(fm, torch, dev, which, steps):
+    """A few plain launches of one workload (warm-up included), for ncu captures."""
+    if which.startswith("hadamard"):
+        xf, xi = I.hadamard_block()
+        mode = {"hadamard": fm.FM_HAD_FP32, "hadamard_int8": fm.FM_HAD_INT8, "hadamard_bf16": fm.FM_HAD_BF16X2}[which]
+        X = torch.from_numpy(xi if mode == fm.FM_HAD_INT8 else xf).to(dev)
+        A = fm.hadamard(LOG2N, mode)
+        fn = lambda: A.forward(X)
+    elif which == "cs":
+        c, d, idx, X, _, _ = I.cs_operator()
+        A = fm.product(fm.partial(idx, len(c)), fm.diag(d), fm.circulant(c))
+        Xg = torch.from_numpy(X).to(dev)
+        fn = lambda: A.backward(A.forward(Xg))
+    elif which == "kron":
+        ck, Xk, _ = I.kron_large()
+        A = fm.kron(fm.hadamard(8), fm.circulant(ck), fm.fourier(64))
+        Xg = torch.from_numpy(Xk).to(dev)
+        fn = lambda: A.backward(A.forward(Xg))
+    elif which == "circulant_c128":
+        c0, X0, _ = I.circulant_tiny()
+        A = fm.circulant(c0)
+        Xg = torch.from_numpy(X0).to(dev)
+        fn = lambda: A.backward(A.forward(Xg))
+    else:
+        insts = [I.fista_instance(j) for j in range(512)]
+        ops = [fm.product(fm.partial(it["idx"], it["n"]), fm.toeplitz(it["t"], it["n"], it["n"])) for it in insts]
+        b = torch.from_numpy(np.concatenate([I.fista_measurements(it) for it in insts])).to(dev)
+        B = fm.FistaBatch(ops)
+        fn = lambda: B.solve(b)
+    for _ in range(max(1, steps)):
+        fn()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": which, "runs": max(1, steps), "launches": fm.launch_count()}))
+
+
+def measure_fista(fm, torch, dev, stream, cpu_sample=True):
+    """Batched FISTA: 4096 instances, n ~ U{2^10..2^14}, 200 steps, one persistent launch
+    replayed from a CUDA graph, against the same kernel launched once per instance."""
+    insts = [I.fista_instance(j) for j in range(FISTA_INSTANCES)]
+    ops = [fm.product(fm.partial(it["idx"], it["n"]), fm.toeplitz(it["t"], it["n"], it["n"])) for it in insts]
+    b = torch.from_numpy(np.concatenate([I.fista_measurements(it) for it in insts])).to(dev)
+    B = fm.FistaBatch(ops)
+    x = torch.empty(B.total_cols, dtype=torch.float32, device=dev)
+    B.solve(b, x=x)                       # warm-up
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        B.solve(b, x=x)
+    g.replay()
+    torch.cuda.synchronize()
+    reps = 3
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        g.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) / 1e3 / reps
+    # one instance per launch, on a sample of the batch (same kernel, one CTA per launch)
+    sample = 256
+    Bs = fm.FistaBatch(ops[:sample])
+    bs = b[:Bs.total_rows]
+    Bs.solve(bs, mode=1)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    Bs.solve(bs, mode=1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_single = e0.elapsed_time(e1) / 1e3
+    row = {"solves/s": FISTA_INSTANCES / t_batch, "ms_per_batch": t_batch * 1e3, "instances": FISTA_INSTANCES,
+           "iterations": 200, "graph": True,
+           "per_instance_launch_solves/s": sample / t_single, "per_instance_launch_sample": sample,
+           "speedup_vs_per_instance_launch": (FISTA_INSTANCES / t_batch) / (sample / t_single),
+           "accuracy": "rel err <= 1e-4 vs the FP64 oracle (tests/test_gpu_fista.py)"}
+    if cpu_sample:
+        import oracle as O
+        t0, done = time.perf_counter(), 0
+        while time.perf_counter() - t0 < 10.0 and done < 64:
+            it = insts[done]
+            bb = I.fista_measurements(it).astype(np.float64)
+            A, lam, L = O.fista_problem(it, bb)
+            O.fista(A, bb, lam, L, iters=200)
+            done += 1
+        row["cpu_oracle_solves/s"] = done / (time.perf_counter() - t0)
+        row["cpu_oracle_sample"] = f"first {done} instances, 1 core, FP64 numpy"
+    return row
 
 
 if __name__ == "__main__":
