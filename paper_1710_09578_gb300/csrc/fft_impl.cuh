@@ -210,158 +210,7 @@ __device__ __forceinline__ void spec_mul(C (&r)[EPT], const C* __restrict__ spec
     default: { CALL(2); } break; \
   }
 
-template <typename T, int THREADS, int EPT>
-__global__ void __launch_bounds__(THREADS) fft_tile_kernel(const __grid_constant__ FftArgs<T> a) {
-  typedef typename Cx<T>::t C;
-  constexpr int E = THREADS * EPT;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* s = reinterpret_cast<C*>(smem_raw);
-  // per-vector table after the padded tile, on a 16-byte boundary (it holds int64 fields)
-  VecInfo* vinfo = reinterpret_cast<VecInfo*>(smem_raw + fft_vinfo_offset<C>(E));
-  const int logL = a.logL, logV = a.logV, vfast = a.vfast, V = a.V;
-  const int64_t g0 = (int64_t)blockIdx.x * V;
-  const int64_t nvec = a.ncu * a.outer * a.inner;
-
-  // ---- per-vector addressing
-  for (int v = threadIdx.x; v < V; v += THREADS) {
-    VecInfo vi;
-    const int64_t g = g0 + v;
-    if (g < nvec) {
-      const int64_t i = g % a.inner, q = g / a.inner;
-      const int64_t o = q % a.outer, c = q / a.outer;
-      const int64_t oi = o * a.inner + i;
-      const int64_t cin = a.in_mode == IO_RP ? 2 * c : c;
-      const int64_t cout = a.out_mode == IO_RP ? 2 * c : c;
-      vi.in_off = cin * a.in_ld + o * a.in_ostride + (i % a.in_imod);
-      vi.out_off = cout * a.out_ld + o * a.out_ostride + (i % a.out_imod);
-      vi.in_n2 = (int32_t)((oi / a.in_fdiv) % a.in_fmod);
-      vi.out_n2 = (int32_t)((oi / a.out_fdiv) % a.out_fmod);
-      vi.tw_n2 = (int32_t)((oi / a.tw_div) % a.tw_mod);
-      vi.flags = (2 * c + 1 < a.ncols) ? 1 : 0;
-      vi.soff = a.spec_omod > 1 ? ((o % a.spec_omod) << logL) : 0;
-    } else {
-      vi.in_off = -1;
-      vi.out_off = -1;
-      vi.in_n2 = vi.out_n2 = vi.tw_n2 = 0;
-      vi.flags = 0;
-      vi.soff = 0;
-    }
-    vinfo[v] = vi;
-  }
-  __syncthreads();
-
-  // ---- load, staged through shared memory in the order that is contiguous in HBM
-  for (int e = threadIdx.x; e < E; e += THREADS) {
-    int t, v;
-    if (a.in_vcontig) { v = e & (V - 1); t = e >> logV; }
-    else { t = e & ((1 << logL) - 1); v = e >> logL; }
-    s[spad(lin_index(t, v, logL, logV, vfast))] = fft_load<T>(a, vinfo[v], t);
-  }
-  __syncthreads();
-
-  C r[EPT];
-  const int R0 = a.rad[0];
-#define LS(RR) regs_from_smem<RR, THREADS, EPT, C>(r, s, logL, logV, vfast)
-  FM_RADIX_SWITCH(R0, LS)
-
-  // ---- passes: forward (dir0) and, for a convolution, spectrum product + inverse
-  int Rlast = R0;
-  const int nseg = a.conv ? 2 : 1;
-  for (int seg = 0; seg < nseg; ++seg) {
-    const int dir = seg == 0 ? a.dir0 : -a.dir0;
-    int logNs = 0;
-    for (int p = 0; p < a.nrad; ++p) {
-      const int R = seg == 0 ? a.rad[p] : a.rad[a.nrad - 1 - p];
-#define PC(RR) pass_compute<RR, THREADS, EPT, C>(r, logL, logV, vfast, logNs, dir, a.tw)
-      FM_RADIX_SWITCH(R, PC)
-#undef PC
-      Rlast = R;
-      if (p + 1 == a.nrad) break;
-      __syncthreads();
-#define PS(RR) regs_to_smem<RR, THREADS, EPT, C>(r, s, logL, logV, vfast, logNs)
-      FM_RADIX_SWITCH(R, PS)
-#undef PS
-      __syncthreads();
-      const int Rn = seg == 0 ? a.rad[p + 1] : a.rad[a.nrad - 2 - p];
-      FM_RADIX_SWITCH(Rn, LS)
-      logNs += (R == 8 ? 3 : (R == 4 ? 2 : 1));
-    }
-    if (seg == 0 && a.conv) {
-#define SPM(RR) spec_mul<RR, THREADS, EPT, C>(r, a.spec, a.spec_conj, vinfo, logL, logV, vfast)
-      FM_RADIX_SWITCH(Rlast, SPM)
-#undef SPM
-    }
-  }
-#undef LS
-
-  // ---- store, staged through shared memory
-  __syncthreads();
-  const int logLast = logL - (Rlast == 8 ? 3 : (Rlast == 4 ? 2 : 1));
-#define ST(RR) regs_to_smem<RR, THREADS, EPT, C>(r, s, logL, logV, vfast, logLast)
-  FM_RADIX_SWITCH(Rlast, ST)
-#undef ST
-  __syncthreads();
-  for (int e = threadIdx.x; e < E; e += THREADS) {
-    int t, v;
-    if (a.out_vcontig) { v = e & (V - 1); t = e >> logV; }
-    else { t = e & ((1 << logL) - 1); v = e >> logL; }
-    fft_store<T>(a, vinfo[v], t, s[spad(lin_index(t, v, logL, logV, vfast))]);
-  }
-}
-
-// ------------------------------------------------------------------ host side
-template <typename T, int THREADS, int EPT>
-static fm_status launch_cfg(FftArgs<T> a, cudaStream_t st) {
-  typedef typename Cx<T>::t C;
-  constexpr int E = THREADS * EPT;
-  a.V = (int)(E >> a.logL);
-  a.logV = 0;
-  while ((1 << a.logV) < a.V) ++a.logV;
-  const int64_t nvec = a.ncu * a.outer * a.inner;
-  const int64_t tiles = (nvec + a.V - 1) / a.V;
-  if (tiles > 0x7fffffffLL) { set_error("fft: too many tiles"); return FM_ERR_UNSUPPORTED; }
-  // vectors adjacent in HBM: consecutive inner index, or unit outer stride
-  a.in_vcontig = (a.inner > 1 || a.in_ostride == 1) ? 1 : 0;
-  a.out_vcontig = (a.inner > 1 || a.out_ostride == 1) ? 1 : 0;
-  // passes run with vectors fastest when a tile holds enough of them
-  a.vfast = a.V >= 16 ? 1 : 0;
-  const size_t smem = fft_vinfo_offset<C>(E) + (size_t)a.V * sizeof(VecInfo);
-  auto kern = fft_tile_kernel<T, THREADS, EPT>;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  static std::atomic<unsigned long long> attr_bytes[32];
-  if (dev < 32 && attr_bytes[dev].load() < smem) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) { set_error("fft smem attribute: %s", cudaGetErrorString(e)); return FM_ERR_CUDA; }
-    attr_bytes[dev].store(smem);
-  }
-  kern<<<(unsigned)tiles, THREADS, smem, st>>>(a);
-  return after_launch("fft_tile_kernel");
-}
-
 template <typename T>
 int fft_max_tile() { return sizeof(T) == 4 ? 16384 : 8192; }
-
-template <typename T>
-fm_status fft_launch(FftArgs<T> a, cudaStream_t st) {
-  if (a.L < 2 || (a.L & (a.L - 1)) || a.L > fft_max_tile<T>()) {
-    set_error("fft: unsupported single-tile length %lld", (long long)a.L);
-    return FM_ERR_UNSUPPORTED;
-  }
-  a.logL = 0;
-  while ((1LL << a.logL) < a.L) ++a.logL;
-  // radix schedule: 8s, then one 4 or 2
-  a.nrad = 0;
-  int rem = a.logL;
-  while (rem >= 3) { a.rad[a.nrad++] = 8; rem -= 3; }
-  if (rem == 2) a.rad[a.nrad++] = 4;
-  if (rem == 1) a.rad[a.nrad++] = 2;
-  if (a.ncu * a.outer * a.inner == 0) return FM_OK;
-  if (a.L <= 4096) return launch_cfg<T, 256, 16>(a, st);
-  if (a.L <= 8192) return launch_cfg<T, 512, 16>(a, st);
-  if constexpr (sizeof(T) == 4) return launch_cfg<T, 512, 32>(a, st);
-  set_error("fft: length %lld", (long long)a.L);
-  return FM_ERR_UNSUPPORTED;
-}
 
 }  // namespace fm

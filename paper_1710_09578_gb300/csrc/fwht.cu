@@ -175,100 +175,88 @@ __global__ void __launch_bounds__(THREADS) fwht_tile_kernel(const __grid_constan
 // n = C * 2^14 with plain column blocks (f32 or int8 -> int32).  CTA r of a column owns
 // block r (2^14 elements, 64 KB of FP32/int32 in shared memory) and 512 threads with 32
 // elements each.  Element e of the block has bits 0..13; the transform is done in three
-// register rounds over bit groups {0,1,11,12,13}, {2..6} and {7..10} with two shared-memory
-// exchanges in between; the first round loads straight from HBM (16-byte vectors, all the
-// C blocks combined with row r of H_C as they arrive) and the last round stores straight
-// to HBM (each warp writes 128 contiguous bytes per instruction).
-// Shared-memory word of element e: e ^ (((e >> 7) & 31) << 2), which keeps 16-byte groups
-// intact and makes every access pattern below bank-conflict free.
-__device__ __forceinline__ int lswz(int e) { return e ^ (((e >> 7) & 31) << 2); }
+// register rounds over bit groups {0,1,2,12,13}, {3..7} and {8..11} with two shared-memory
+// exchanges in between.  The first round loads straight from HBM with one 32-byte vector
+// load per block and register group (all C blocks combined with row r of H_C as they
+// arrive); the last round stores straight to HBM (128 contiguous bytes per warp and
+// instruction).  Shared-memory word of element e: e ^ (((e >> 8) & 3) << 3), which keeps
+// 32-byte groups intact and makes the round-B and round-C accesses bank-conflict free.
+__device__ __forceinline__ int lswz(int e) { return e ^ (((e >> 8) & 3) << 3); }
 
 template <typename W> struct Vec4;
 template <> struct Vec4<float> { typedef float4 t; };
 template <> struct Vec4<int> { typedef int4 t; };
 
-__device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
-__device__ __forceinline__ int4 ld4(const int* p) { return __ldg(reinterpret_cast<const int4*>(p)); }
-__device__ __forceinline__ int4 ld4(const int8_t* p) {
-  const char4 c = __ldg(reinterpret_cast<const char4*>(p));
-  return make_int4(c.x, c.y, c.z, c.w);
+__device__ __forceinline__ void ld8(const float* p, float (&v)[8]) {
+  asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+               : "l"(p));
+}
+__device__ __forceinline__ void ld8(const int8_t* p, int (&v)[8]) {
+  const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    v[i] = (int)(int8_t)((u.x >> (8 * i)) & 0xff);
+    v[4 + i] = (int)(int8_t)((u.y >> (8 * i)) & 0xff);
+  }
 }
 __device__ __forceinline__ float4 make_vec4(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
 __device__ __forceinline__ int4 make_vec4(int a, int b, int c, int d) { return make_int4(a, b, c, d); }
 
-template <typename V> __device__ __forceinline__ void acc4(V& a, const V& b, bool neg) {
-  if (neg) { a.x -= b.x; a.y -= b.y; a.z -= b.z; a.w -= b.w; }
-  else { a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w; }
-}
-
 template <typename Tin, typename W, int C>
 __global__ void __launch_bounds__(512, 2) fwht_long_kernel(const Tin* __restrict__ in, int64_t in_ld,
-                                                           W* __restrict__ out, int64_t out_ld, int beta,
-                                                           int nparts) {
+                                                           W* __restrict__ out, int64_t out_ld, int beta) {
   typedef typename Vec4<W>::t V4;
   constexpr int LP = 1 << 14;
-  __shared__ __align__(16) W s[LP];
-  // C > 1: CTA `part` combines the C blocks of its column with row `part` of H_C.
-  // C == 1: CTA `part` transforms block `part` of nparts on its own.
-  const int np = C > 1 ? C : nparts;
-  const int part = (int)(blockIdx.x % np);
-  const int64_t col = blockIdx.x / np;
+  __shared__ __align__(32) W s[LP];
+  const int part = (int)(blockIdx.x % C);
+  const int64_t col = blockIdx.x / C;
   const int t = threadIdx.x;
-  const Tin* x = in + col * in_ld + (C > 1 ? 0 : (int64_t)part * LP);
+  const Tin* x = in + col * in_ld + 8 * t;
   W r[32];
 
-  // round A: e = c + 4 t + 2048 q, registers hold bits {0,1} (c) and {11,12,13} (q)
-  {
-    V4 acc[8];
+  // round A: e = c + 8 t + 4096 q, registers hold bits {0,1,2} (c) and {12,13} (q)
 #pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = ld4(x + 4 * t + 2048 * q);
+  for (int q = 0; q < 4; ++q) ld8(x + 4096 * q, *reinterpret_cast<W(*)[8]>(&r[8 * q]));
 #pragma unroll
-    for (int sb = 1; sb < C; ++sb) {
-      const bool neg = __popc(sb & part) & 1;
+  for (int sb = 1; sb < C; ++sb) {
+    const bool neg = __popc(sb & part) & 1;
 #pragma unroll
-      for (int hq = 0; hq < 8; hq += 4) {
-        V4 v[4];
+    for (int q = 0; q < 4; ++q) {
+      W v[8];
+      ld8(x + (int64_t)sb * LP + 4096 * q, v);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) v[q] = ld4(x + (int64_t)sb * LP + 4 * t + 2048 * (hq + q));
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc4(acc[hq + q], v[q], neg);
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      r[4 * q + 0] = acc[q].x;
-      r[4 * q + 1] = acc[q].y;
-      r[4 * q + 2] = acc[q].z;
-      r[4 * q + 3] = acc[q].w;
+      for (int c = 0; c < 8; ++c) r[8 * q + c] = neg ? r[8 * q + c] - v[c] : r[8 * q + c] + v[c];
     }
   }
   wht_regs<W, 32>(r);
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int e = 4 * t + 2048 * q;
-    *reinterpret_cast<V4*>(&s[lswz(e)]) = make_vec4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+  for (int q = 0; q < 4; ++q) {
+    W* p = &s[lswz(8 * t + 4096 * q)];
+    *reinterpret_cast<V4*>(p) = make_vec4(r[8 * q], r[8 * q + 1], r[8 * q + 2], r[8 * q + 3]);
+    *reinterpret_cast<V4*>(p + 4) = make_vec4(r[8 * q + 4], r[8 * q + 5], r[8 * q + 6], r[8 * q + 7]);
   }
   __syncthreads();
 
-  // round B: e = a + 4 k + 128 b with a = t & 3, b = t >> 2; registers hold bits 2..6 (k)
+  // round B: e = a + 8 k + 256 b with a = t & 7, b = t >> 3; registers hold bits 3..7 (k)
   {
-    const int base = (t & 3) + 128 * (t >> 2);
+    const int base = (t & 7) + 256 * (t >> 3);
 #pragma unroll
-    for (int k = 0; k < 32; ++k) r[k] = s[lswz(base + 4 * k)];
+    for (int k = 0; k < 32; ++k) r[k] = s[lswz(base + 8 * k)];
     wht_regs<W, 32>(r);
 #pragma unroll
-    for (int k = 0; k < 32; ++k) s[lswz(base + 4 * k)] = r[k];
+    for (int k = 0; k < 32; ++k) s[lswz(base + 8 * k)] = r[k];
   }
   __syncthreads();
 
-  // round C: e = l + 128 m + 2048 h with l = t & 127, h = 2 (t >> 7) + g; registers hold
-  // bits 7..10 (m) for g = 0, 1
+  // round C: e = l + 256 m + 4096 h with l = t & 255, h = 2 (t >> 8) + g; registers hold
+  // bits 8..11 (m) for g = 0, 1
   {
-    const int l = t & 127, h0 = 2 * (t >> 7);
+    const int l = t & 255, h0 = 2 * (t >> 8);
 #pragma unroll
     for (int g = 0; g < 2; ++g)
 #pragma unroll
-      for (int m = 0; m < 16; ++m) r[16 * g + m] = s[lswz(l + 128 * m + 2048 * (h0 + g))];
+      for (int m = 0; m < 16; ++m) r[16 * g + m] = s[lswz(l + 256 * m + 4096 * (h0 + g))];
     wht_regs<W, 16>(r);
     wht_regs<W, 16>(r + 16);
     W* y = out + col * out_ld + (int64_t)part * LP;
@@ -276,7 +264,7 @@ __global__ void __launch_bounds__(512, 2) fwht_long_kernel(const Tin* __restrict
     for (int g = 0; g < 2; ++g)
 #pragma unroll
       for (int m = 0; m < 16; ++m) {
-        W* p = y + l + 128 * m + 2048 * (h0 + g);
+        W* p = y + l + 256 * m + 4096 * (h0 + g);
         *p = beta ? *p + r[16 * g + m] : r[16 * g + m];
       }
   }
@@ -287,12 +275,12 @@ static fm_status fwht_long(const FwhtArgs& a, cudaStream_t st) {
   const int logC = a.logL - 14;
   const Tin* in = reinterpret_cast<const Tin*>(a.in);
   W* out = reinterpret_cast<W*>(a.out);
-  if (a.ncols == 0) return FM_OK;
   const int64_t blocks = a.ncols << logC;
+  if (blocks == 0) return FM_OK;
   switch (logC) {
-    case 0: fwht_long_kernel<Tin, W, 1><<<(unsigned)blocks, 512, 0, st>>>(in, a.in_ld, out, a.out_ld, a.beta, 1); break;
-    case 1: fwht_long_kernel<Tin, W, 2><<<(unsigned)blocks, 512, 0, st>>>(in, a.in_ld, out, a.out_ld, a.beta, 2); break;
-    case 2: fwht_long_kernel<Tin, W, 4><<<(unsigned)blocks, 512, 0, st>>>(in, a.in_ld, out, a.out_ld, a.beta, 4); break;
+    case 0: fwht_long_kernel<Tin, W, 1><<<(unsigned)blocks, 512, 0, st>>>(in, a.in_ld, out, a.out_ld, a.beta); break;
+    case 1: fwht_long_kernel<Tin, W, 2><<<(unsigned)blocks, 512, 0, st>>>(in, a.in_ld, out, a.out_ld, a.beta); break;
+    case 2: fwht_long_kernel<Tin, W, 4><<<(unsigned)blocks, 512, 0, st>>>(in, a.in_ld, out, a.out_ld, a.beta); break;
     default: set_error("fwht_long: unsupported length"); return FM_ERR_UNSUPPORTED;
   }
   return after_launch("fwht_long_kernel");
@@ -302,8 +290,9 @@ static fm_status fwht_long(const FwhtArgs& a, cudaStream_t st) {
 static bool long_path_ok(const FwhtArgs& a, int in_size) {
   if (a.logL < 14 || a.logL > 16 || a.outer != 1 || a.inner != 1) return false;
   if (a.in_tstride != 1 || a.out_tstride != 1) return false;
-  if (((uintptr_t)a.in % (4 * in_size)) || ((uintptr_t)a.out % 16)) return false;
-  if ((a.in_ld * in_size) % (4 * in_size) || (a.out_ld * 4) % 16) return false;
+  // 8-element (32 B for FP32, 8 B for int8) vector loads, 16-byte output words
+  if (((uintptr_t)a.in % (8 * in_size)) || ((uintptr_t)a.out % 16)) return false;
+  if (a.in_ld % 8 || a.out_ld % 4) return false;
   return true;
 }
 
