@@ -213,8 +213,8 @@ void fm_batch_release(fm_batch B);
 fm_status fm_batch_sizes(fm_batch B, int64_t* total_rows, int64_t* total_cols);
 
 /* Solve every instance.  b: packed float32 measurements (instance i at offset
- * sum_{j<i} m_j), x: packed float32 solutions (offset sum_{j<i} n_j), both device
- * buffers.  No allocation and no host synchronisation: capturable in a CUDA graph. */
+ * sum_{j<i} m_j), x: packed float32 solutions (offset sum_{j<i} n_j, 8-byte aligned), both
+ * device buffers.  No allocation and no host synchronisation: capturable in a CUDA graph. */
 fm_status fm_fista(fm_batch B, const float* b, float* x, const fm_fista_params* p,
                    const fm_fista_report* rep, void* stream);
 

@@ -26,7 +26,7 @@
 #include <vector>
 
 #include "exec.h"
-#include "fft_impl.cuh"
+#include "fft2.cuh"
 #include "pointwise.h"
 
 namespace fm {
@@ -34,6 +34,7 @@ namespace fm {
 struct FInst {
   const float2* spec;   // FFT_L(c) / L of the circulant embedding (L = 2n entries)
   const int32_t* idx;   // m selected rows
+  const int32_t* inv;   // n entries: r if row r selects position j, else -1
   int64_t b_off;        // offset of b_i in the packed b
   int64_t x_off;        // offset of x_i in the packed x (and of y_i in the scratch)
   int n, m, logn, pad;
@@ -65,12 +66,13 @@ struct FistaArgs {
   int* counter;
 };
 
-constexpr int kFThreads = 512, kFEpt = 32, kFE = kFThreads * kFEpt;  // 2^14 complex per tile
-constexpr int kFMaxV = 64;                                               // n >= 256
+constexpr int kFThreads = 1024, kFEpt = 16, kFE = kFThreads * kFEpt;  // 2^14 complex per tile
+constexpr int kFMaxV = 64;                                                // n >= 256
 
 struct VState {
   const float2* spec;
   const int32_t* idx;
+  const int32_t* inv;
   int64_t b_off, x_off;
   int m, valid, inst, pad;
   float invL, thr;
@@ -78,8 +80,20 @@ struct VState {
   unsigned amax;
 };
 
-__device__ __forceinline__ float2* zaddr(float2* s, int t, int v, int logL, int logV, int vfast) {
-  return &s[spad(lin_index(t, v, logL, logV, vfast))];
+// Tile geometry of a group with transform length 2^LOGL: V = 2^(14 - LOGL) vectors.
+template <int LOGL>
+struct FGeo {
+  static constexpr int LOGV = 14 - LOGL, V = 1 << LOGV, NC = 1 << LOGL;
+};
+
+// x and y are rewritten by the kernel itself: read and write them through L2 (.cg), never
+// through the read-only path.
+__device__ __forceinline__ float2 ld_state(const float* p) { return __ldcg(reinterpret_cast<const float2*>(p)); }
+__device__ __forceinline__ void st_state(float* p, float2 v) { __stcg(reinterpret_cast<float2*>(p), v); }
+
+template <int LOGL>
+__device__ __forceinline__ float2* zaddr(float2* s, int t, int v) {
+  return &s[sp2<LOGL, FGeo<LOGL>::LOGV>(t, v)];
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -88,7 +102,7 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Add val into red[v]; one atomic per warp when the whole warp works on the same vector.
+// Add val into vs[v].acc; one atomic per warp when the whole warp works on the same vector.
 __device__ __forceinline__ void vec_add(VState* vs, int v, double val) {
   const int v0 = __shfl_sync(0xffffffffu, v, 0);
   if (__all_sync(0xffffffffu, v == v0)) {
@@ -103,42 +117,32 @@ __device__ __forceinline__ void vec_max(VState* vs, int v, float val) {
   atomicMax(&vs[v].amax, __float_as_uint(fabsf(val)));
 }
 
-// Natural-order FFT of every vector of the tile, in place in shared memory.
-__device__ __noinline__ void tile_fft(float2* s, int logL, int logV, int vfast, int dir, const float2* tw) {
-  int rad[6], nrad = 0, rem = logL;
-  while (rem >= 3) { rad[nrad++] = 8; rem -= 3; }
-  if (rem == 2) rad[nrad++] = 4;
-  if (rem == 1) rad[nrad++] = 2;
+// Natural-order FFT of every vector of the tile, in place in shared memory (passes of the
+// compile-time engine).  Entry and exit: synchronised, natural order in shared memory.
+template <int LOGL>
+__device__ __forceinline__ void tile_fft(float2* s, int dir, const float2* tw) {
+  constexpr int LOGV = FGeo<LOGL>::LOGV;
+  using S = Sched<LOGL>;
+  constexpr int LR0 = S::lr(0), LRL = S::lr(S::NR - 1);
   float2 r[kFEpt];
-  int logNs = 0;
-  for (int p = 0; p < nrad; ++p) {
-    const int R = rad[p];
-#define FLS(RR) regs_from_smem<RR, kFThreads, kFEpt, float2>(r, s, logL, logV, vfast)
-    FM_RADIX_SWITCH(R, FLS)
-#undef FLS
-    __syncthreads();
-#define FPC(RR) pass_compute<RR, kFThreads, kFEpt, float2>(r, logL, logV, vfast, logNs, dir, tw)
-    FM_RADIX_SWITCH(R, FPC)
-#undef FPC
-#define FPS(RR) regs_to_smem<RR, kFThreads, kFEpt, float2>(r, s, logL, logV, vfast, logNs)
-    FM_RADIX_SWITCH(R, FPS)
-#undef FPS
-    __syncthreads();
-    logNs += R == 8 ? 3 : (R == 4 ? 2 : 1);
-  }
+  p2_read<float2, kFThreads, kFEpt, LOGL, LOGV, LR0>(r, s);
+  p2_run<float2, kFThreads, kFEpt, LOGL, LOGV, 0, false>(r, s, dir, tw);
+  __syncthreads();
+  p2_write<float2, kFThreads, kFEpt, LOGL, LOGV, LRL, LOGL - LRL>(r, s);
+  __syncthreads();
 }
 
 // Z <- pre-step( spectrum x post-step(Z) ) for every vector: see the file comment.
-__device__ void tile_spectral(float2* s, VState* vs, int logL, int logV, int vfast, int adjoint,
-                              const float2* tw2) {
-  const int Nc = 1 << logL, half = Nc >> 1, V = 1 << logV;
-  const int tsh = 14 - logL;  // index scale into the W_{2^15} table for exp(-2 pi i k / (2 Nc))
+template <int LOGL>
+__device__ void tile_spectral(float2* s, VState* vs, int adjoint, const float2* tw2) {
+  constexpr int Nc = 1 << LOGL, half = Nc >> 1, V = FGeo<LOGL>::V;
+  constexpr int tsh = 14 - LOGL;  // index scale into the W_{2^15} table for exp(-2 pi i k / (2 Nc))
   for (int q = threadIdx.x; q < V * half; q += kFThreads) {
-    const int v = q >> (logL - 1), k = q & (half - 1);
+    const int v = q >> (LOGL - 1), k = q & (half - 1);
     if (!vs[v].valid) continue;
     const int kp = Nc - k;
-    float2* pk = zaddr(s, k, v, logL, logV, vfast);
-    float2* pm = zaddr(s, kp & (Nc - 1), v, logL, logV, vfast);
+    float2* pk = zaddr<LOGL>(s, k, v);
+    float2* pm = zaddr<LOGL>(s, kp & (Nc - 1), v);
     const float2 Zk = *pk, Zm = *pm;
     // E = (Zk + conj Zm)/2, O = (Zk - conj Zm)/(2i)
     const float2 E = make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y));
@@ -160,75 +164,211 @@ __device__ void tile_spectral(float2* s, VState* vs, int logL, int logV, int vfa
   // k = Nc / 2 pairs with itself: Z' = conj(c') Z with c' = 2 spec (conjugated for T^T)
   for (int v = threadIdx.x; v < V; v += kFThreads) {
     if (!vs[v].valid) continue;
-    float2* p = zaddr(s, half, v, logL, logV, vfast);
+    float2* p = zaddr<LOGL>(s, half, v);
     float2 c = cscale(vs[v].spec[half], 2.f);
     if (adjoint) c = cconj(c);
     *p = cmul(cconj(c), *p);
   }
 }
 
-__device__ __forceinline__ float unpack(const float2* s, int m, int v, int logL, int logV, int vfast) {
-  const float2 z = s[spad(lin_index(m >> 1, v, logL, logV, vfast))];
+template <int LOGL>
+__device__ __forceinline__ float unpack(const float2* s, int m, int v) {
+  const float2 z = s[sp2<LOGL, FGeo<LOGL>::LOGV>(m >> 1, v)];
   return (m & 1) ? z.y : z.x;
 }
 
 // Z <- pack([w; 0]) where w is the length-n real vector at src + x_off of each vector
-__device__ void pack_from(float2* s, VState* vs, const float* src, int logL, int logV, int vfast) {
-  const int Nc = 1 << logL, V = 1 << logV;
+template <int LOGL>
+__device__ void pack_from(float2* s, VState* vs, const float* src) {
+  constexpr int Nc = 1 << LOGL, V = FGeo<LOGL>::V;
   for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
-    const int v = q >> logL, k = q & (Nc - 1);
+    const int v = q >> LOGL, k = q & (Nc - 1);
     float2 z = make_float2(0.f, 0.f);
+    if (vs[v].valid && k < (Nc >> 1)) z = ld_state(src + vs[v].x_off + 2 * k);
+    *zaddr<LOGL>(s, k, v) = z;
+  }
+}
+
+// tile <- T w (adjoint: T^T w) for the packed w in the tile
+template <int LOGL>
+__device__ void apply_T(float2* s, VState* vs, int adjoint, const float2* tw, const float2* tw2) {
+  __syncthreads();
+  tile_fft<LOGL>(s, -1, tw);
+  tile_spectral<LOGL>(s, vs, adjoint, tw2);
+  __syncthreads();
+  tile_fft<LOGL>(s, +1, tw);
+}
+
+// In place on the tile, which holds T w unpacked as pairs (w[2k], w[2k+1]) at position k:
+// u = P^T (P T w - b) (MODE_RESID), u = P^T P T w (MODE_MASK) or u = P^T b (MODE_B), packed
+// the same way for the next transform, zeros in the upper half; with sumsq the squares of
+// the selected entries are added into vs[v].acc.
+enum { MODE_MASK = 0, MODE_RESID = 1, MODE_B = 2 };
+template <int LOGL, int MODE>
+__device__ void mask_rows(float2* s, VState* vs, const float* b, bool sumsq) {
+  constexpr int Nc = 1 << LOGL, V = FGeo<LOGL>::V;
+  for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
+    const int v = q >> LOGL, k = q & (Nc - 1);
+    float2* p = zaddr<LOGL>(s, k, v);
+    float2 u = make_float2(0.f, 0.f);
+    double ss = 0.0;
     if (vs[v].valid && k < (Nc >> 1)) {
-      const float* w = src + vs[v].x_off;
-      z = make_float2(w[2 * k], w[2 * k + 1]);
+      const float2 z = MODE == MODE_B ? make_float2(0.f, 0.f) : *p;
+      const int2 r = *reinterpret_cast<const int2*>(vs[v].inv + 2 * k);
+      const float* bb = b + vs[v].b_off;
+      if (r.x >= 0) u.x = MODE == MODE_B ? bb[r.x] : (MODE == MODE_RESID ? z.x - bb[r.x] : z.x);
+      if (r.y >= 0) u.y = MODE == MODE_B ? bb[r.y] : (MODE == MODE_RESID ? z.y - bb[r.y] : z.y);
+      ss = (double)u.x * (double)u.x + (double)u.y * (double)u.y;
     }
-    *zaddr(s, k, v, logL, logV, vfast) = z;
+    *p = u;
+    if (sumsq) vec_add(vs, v, ss);
   }
 }
 
-// phi: tile holds T w after the call (unpacked on demand); returns nothing
-__device__ void apply_T(float2* s, VState* vs, int logL, int logV, int vfast, int adjoint, const float2* tw,
-                        const float2* tw2) {
-  __syncthreads();
-  tile_fft(s, logL, logV, vfast, -1, tw);
-  tile_spectral(s, vs, logL, logV, vfast, adjoint, tw2);
-  __syncthreads();
-  tile_fft(s, logL, logV, vfast, +1, tw);
-}
-
-template <bool FISTA_RESID>
-__device__ void gather_rows(float (&rr)[kFEpt], const float2* s, VState* vs, const float* b, int logL, int logV,
-                            int vfast, bool sumsq) {
-  const int Nc = 1 << logL, V = 1 << logV;
-#pragma unroll
-  for (int i = 0; i < kFEpt; ++i) {
-    const int q = threadIdx.x + i * kFThreads;
-    const int v = q >> logL, j = q & (Nc - 1);
-    float r = 0.f;
-    if (q < V * Nc && vs[v].valid && j < vs[v].m) {
-      r = unpack(s, vs[v].idx[j], v, logL, logV, vfast);
-      if (FISTA_RESID) r -= b[vs[v].b_off + j];
+// Every step of one group: lambda, L, K FISTA steps and the objective.
+template <int LOGL>
+__device__ void fista_group(const FistaArgs& a, const FGroup& G, float2* s, VState* vs, double* s_t) {
+  constexpr int Nc = 1 << LOGL, V = FGeo<LOGL>::V;
+  for (int v = threadIdx.x; v < V; v += kFThreads) {
+    VState w = {};
+    w.valid = v < G.count;
+    if (w.valid) {
+      const int ii = a.order[G.first + v];
+      const FInst in = a.inst[ii];
+      w.spec = in.spec;
+      w.idx = in.idx;
+      w.inv = in.inv;
+      w.b_off = in.b_off;
+      w.x_off = in.x_off;
+      w.m = in.m;
+      w.cap = in.cap;
+      w.inst = ii;
     }
-    rr[i] = r;
-    if (sumsq) vec_add(vs, v, (double)r * (double)r);
+    vs[v] = w;
   }
-}
+  __syncthreads();
 
-__device__ void scatter_rows(float2* s, const float (&rr)[kFEpt], VState* vs, int logL, int logV, int vfast) {
-  const int Nc = 1 << logL, V = 1 << logV;
+  // ---- lambda = lambda_rel * ||A^T b||_inf
+  mask_rows<LOGL, MODE_B>(s, vs, a.b, false);
+  apply_T<LOGL>(s, vs, 1, a.tw, a.tw2);
+  for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
+    const int v = q >> LOGL;
+    if (vs[v].valid) vec_max(vs, v, unpack<LOGL>(s, q & (Nc - 1), v));
+  }
   __syncthreads();
-  for (int q = threadIdx.x; q < V * Nc; q += kFThreads) *zaddr(s, q & (Nc - 1), q >> logL, logL, logV, vfast) =
-      make_float2(0.f, 0.f);
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < kFEpt; ++i) {
-    const int q = threadIdx.x + i * kFThreads;
-    const int v = q >> logL, j = q & (Nc - 1);
-    if (q < V * Nc && vs[v].valid && j < vs[v].m) {
-      const int pos = vs[v].idx[j];
-      float* f = reinterpret_cast<float*>(zaddr(s, pos >> 1, v, logL, logV, vfast));
-      f[pos & 1] = rr[i];
+  for (int v = threadIdx.x; v < V; v += kFThreads) vs[v].lam = a.lambda_rel * (double)__uint_as_float(vs[v].amax);
+
+  // ---- power iteration on A^T A from ones / sqrt(n), the iterate kept in y
+  {
+    const float v0 = rsqrtf((float)Nc);
+    for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
+      const int v = q >> LOGL;
+      if (vs[v].valid) __stcg(a.y + vs[v].x_off + (q & (Nc - 1)), v0);
     }
+  }
+  for (int it = 0; it < a.power_iters; ++it) {
+    __syncthreads();
+    pack_from<LOGL>(s, vs, a.y);
+    apply_T<LOGL>(s, vs, 0, a.tw, a.tw2);
+    mask_rows<LOGL, MODE_MASK>(s, vs, a.b, false);
+    apply_T<LOGL>(s, vs, 1, a.tw, a.tw2);
+    for (int v = threadIdx.x; v < V; v += kFThreads) vs[v].acc = 0.0;
+    __syncthreads();
+    for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
+      const int v = q >> LOGL;
+      const float w = unpack<LOGL>(s, q & (Nc - 1), v);
+      vec_add(vs, v, (double)w * (double)w);
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
+      const int v = q >> LOGL;
+      if (vs[v].valid) {
+        const double nrm = sqrt(vs[v].acc);
+        const float w = unpack<LOGL>(s, q & (Nc - 1), v);
+        __stcg(a.y + vs[v].x_off + (q & (Nc - 1)), nrm > 0.0 ? (float)((double)w / nrm) : 0.f);
+      }
+    }
+  }
+  // lam_hat = ||A v||^2, L = min(safety * lam_hat, cap)
+  __syncthreads();
+  for (int v = threadIdx.x; v < V; v += kFThreads) vs[v].acc = 0.0;
+  pack_from<LOGL>(s, vs, a.y);
+  apply_T<LOGL>(s, vs, 0, a.tw, a.tw2);
+  mask_rows<LOGL, MODE_MASK>(s, vs, a.b, true);
+  __syncthreads();
+  for (int v = threadIdx.x; v < V; v += kFThreads) {
+    double L = a.safety * vs[v].acc;
+    if (vs[v].cap < L) L = vs[v].cap;
+    vs[v].L = L;
+    vs[v].invL = L > 0.0 ? (float)(1.0 / L) : 0.f;
+    vs[v].thr = L > 0.0 ? (float)(vs[v].lam / L) : 0.f;
+  }
+  // ---- FISTA from x_0 = y_1 = 0, t_1 = 1; the tile holds pack(y_k) at the top of a step
+  for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
+    const int v = q >> LOGL;
+    if (vs[v].valid) {
+      __stcg(a.x + vs[v].x_off + (q & (Nc - 1)), 0.f);
+      __stcg(a.y + vs[v].x_off + (q & (Nc - 1)), 0.f);
+    }
+    *zaddr<LOGL>(s, q & (Nc - 1), v) = make_float2(0.f, 0.f);
+  }
+  if (threadIdx.x == 0) *s_t = 1.0;
+  for (int k = 0; k < a.iters; ++k) {
+    __syncthreads();
+    const double t = *s_t;
+    const double tn = a.accel ? 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t)) : 1.0;
+    const float beta = a.accel ? (float)((t - 1.0) / tn) : 0.f;
+    apply_T<LOGL>(s, vs, 0, a.tw, a.tw2);
+    mask_rows<LOGL, MODE_RESID>(s, vs, a.b, false);
+    apply_T<LOGL>(s, vs, 1, a.tw, a.tw2);
+    // update: g pairs at positions k < n/2; write x, y and the packed y_{k+1} for the next step
+    for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
+      const int v = q >> LOGL, kk = q & (Nc - 1);
+      float2* p = zaddr<LOGL>(s, kk, v);
+      float2 ny = make_float2(0.f, 0.f);
+      if (vs[v].valid && kk < (Nc >> 1)) {
+        const float2 g = *p;
+        const int64_t o = vs[v].x_off + 2 * kk;
+        const float2 yv = ld_state(a.y + o);
+        const float2 xv = ld_state(a.x + o);
+        const float invL = vs[v].invL, thr = vs[v].thr;
+        const float z0 = yv.x - g.x * invL, z1 = yv.y - g.y * invL;
+        const float m0 = fabsf(z0) - thr, m1 = fabsf(z1) - thr;
+        const float x0 = m0 > 0.f ? copysignf(m0, z0) : 0.f;
+        const float x1 = m1 > 0.f ? copysignf(m1, z1) : 0.f;
+        ny = make_float2(x0 + beta * (x0 - xv.x), x1 + beta * (x1 - xv.y));
+        st_state(a.x + o, make_float2(x0, x1));
+        st_state(a.y + o, ny);
+      }
+      *p = ny;
+    }
+    if (threadIdx.x == 0) *s_t = tn;
+  }
+  // ---- objective 1/2 ||A x - b||^2 + lambda ||x||_1 and status
+  __syncthreads();
+  for (int v = threadIdx.x; v < V; v += kFThreads) vs[v].acc = 0.0;
+  pack_from<LOGL>(s, vs, a.x);
+  apply_T<LOGL>(s, vs, 0, a.tw, a.tw2);
+  mask_rows<LOGL, MODE_RESID>(s, vs, a.b, true);
+  __syncthreads();
+  for (int v = threadIdx.x; v < V; v += kFThreads) vs[v].cap = 0.5 * vs[v].acc;  // reuse cap: data term
+  __syncthreads();
+  for (int v = threadIdx.x; v < V; v += kFThreads) vs[v].acc = 0.0;
+  __syncthreads();
+  for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
+    const int v = q >> LOGL;
+    const float xv = vs[v].valid ? __ldcg(a.x + vs[v].x_off + (q & (Nc - 1))) : 0.f;
+    vec_add(vs, v, fabs((double)xv));
+  }
+  __syncthreads();
+  for (int v = threadIdx.x; v < V; v += kFThreads) {
+    if (!vs[v].valid) continue;
+    const int ii = vs[v].inst;
+    const double obj = vs[v].cap + vs[v].lam * vs[v].acc;
+    if (a.rep_L) a.rep_L[ii] = vs[v].L;
+    if (a.rep_lambda) a.rep_lambda[ii] = vs[v].lam;
+    if (a.rep_obj) a.rep_obj[ii] = obj;
+    if (a.rep_status) a.rep_status[ii] = isfinite(obj) ? 0 : (int)FM_ERR_NUMERIC;
   }
 }
 
@@ -250,153 +390,14 @@ __global__ void __launch_bounds__(kFThreads, 1) fista_kernel(const __grid_consta
     first = false;
     if (gi < 0 || gi >= a.ngroups) break;
     const FGroup G = a.groups[gi];
-    const int logL = G.logn, Nc = 1 << logL;
-    const int logV = 14 - logL, V = 1 << logV;
-    const int vfast = V >= 16 ? 1 : 0;
-    for (int v = threadIdx.x; v < V; v += kFThreads) {
-      VState w = {};
-      w.valid = v < G.count;
-      if (w.valid) {
-        const int ii = a.order[G.first + v];
-        const FInst in = a.inst[ii];
-        w.spec = in.spec;
-        w.idx = in.idx;
-        w.b_off = in.b_off;
-        w.x_off = in.x_off;
-        w.m = in.m;
-        w.cap = in.cap;
-        w.inst = ii;
-      }
-      vs[v] = w;
-    }
-    __syncthreads();
-    float rr[kFEpt];
-
-    // ---- lambda = lambda_rel * ||A^T b||_inf
-    for (int i = 0; i < kFEpt; ++i) {
-      const int q = threadIdx.x + i * kFThreads;
-      const int v = q >> logL, j = q & (Nc - 1);
-      rr[i] = (vs[v].valid && j < vs[v].m) ? a.b[vs[v].b_off + j] : 0.f;
-    }
-    scatter_rows(s, rr, vs, logL, logV, vfast);
-    apply_T(s, vs, logL, logV, vfast, 1, a.tw, a.tw2);
-    __syncthreads();
-    for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
-      const int v = q >> logL;
-      if (vs[v].valid) vec_max(vs, v, unpack(s, q & (Nc - 1), v, logL, logV, vfast));
-    }
-    __syncthreads();
-    for (int v = threadIdx.x; v < V; v += kFThreads) vs[v].lam = a.lambda_rel * (double)__uint_as_float(vs[v].amax);
-
-    // ---- power iteration on A^T A from ones / sqrt(n), the iterate kept in y
-    {
-      const float v0 = rsqrtf((float)Nc);
-      for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
-        const int v = q >> logL;
-        if (vs[v].valid) a.y[vs[v].x_off + (q & (Nc - 1))] = v0;
-      }
-    }
-    for (int it = 0; it < a.power_iters; ++it) {
-      __syncthreads();
-      pack_from(s, vs, a.y, logL, logV, vfast);
-      apply_T(s, vs, logL, logV, vfast, 0, a.tw, a.tw2);
-      __syncthreads();
-      gather_rows<false>(rr, s, vs, a.b, logL, logV, vfast, false);
-      scatter_rows(s, rr, vs, logL, logV, vfast);
-      apply_T(s, vs, logL, logV, vfast, 1, a.tw, a.tw2);
-      for (int v = threadIdx.x; v < V; v += kFThreads) vs[v].acc = 0.0;
-      __syncthreads();
-      for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
-        const int v = q >> logL;
-        const float w = unpack(s, q & (Nc - 1), v, logL, logV, vfast);
-        vec_add(vs, v, (double)w * (double)w);
-      }
-      __syncthreads();
-      for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
-        const int v = q >> logL;
-        if (vs[v].valid) {
-          const double nrm = sqrt(vs[v].acc);
-          const float w = unpack(s, q & (Nc - 1), v, logL, logV, vfast);
-          a.y[vs[v].x_off + (q & (Nc - 1))] = nrm > 0.0 ? (float)((double)w / nrm) : 0.f;
-        }
-      }
-    }
-    // lam_hat = ||A v||^2, L = min(safety * lam_hat, cap)
-    __syncthreads();
-    for (int v = threadIdx.x; v < V; v += kFThreads) vs[v].acc = 0.0;
-    pack_from(s, vs, a.y, logL, logV, vfast);
-    apply_T(s, vs, logL, logV, vfast, 0, a.tw, a.tw2);
-    __syncthreads();
-    gather_rows<false>(rr, s, vs, a.b, logL, logV, vfast, true);
-    __syncthreads();
-    for (int v = threadIdx.x; v < V; v += kFThreads) {
-      double L = a.safety * vs[v].acc;
-      if (vs[v].cap < L) L = vs[v].cap;
-      vs[v].L = L;
-      vs[v].invL = L > 0.0 ? (float)(1.0 / L) : 0.f;
-      vs[v].thr = L > 0.0 ? (float)(vs[v].lam / L) : 0.f;
-    }
-    // ---- FISTA from x_0 = y_1 = 0, t_1 = 1
-    for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
-      const int v = q >> logL;
-      if (vs[v].valid) {
-        a.x[vs[v].x_off + (q & (Nc - 1))] = 0.f;
-        a.y[vs[v].x_off + (q & (Nc - 1))] = 0.f;
-      }
-    }
-    if (threadIdx.x == 0) s_t = 1.0;
-    for (int k = 0; k < a.iters; ++k) {
-      __syncthreads();
-      const double t = s_t;
-      const double tn = a.accel ? 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t)) : 1.0;
-      const float beta = a.accel ? (float)((t - 1.0) / tn) : 0.f;
-      pack_from(s, vs, a.y, logL, logV, vfast);
-      apply_T(s, vs, logL, logV, vfast, 0, a.tw, a.tw2);
-      __syncthreads();
-      gather_rows<true>(rr, s, vs, a.b, logL, logV, vfast, false);
-      scatter_rows(s, rr, vs, logL, logV, vfast);
-      apply_T(s, vs, logL, logV, vfast, 1, a.tw, a.tw2);
-      __syncthreads();
-      for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
-        const int v = q >> logL;
-        if (!vs[v].valid) continue;
-        const int64_t o = vs[v].x_off + (q & (Nc - 1));
-        const float g = unpack(s, q & (Nc - 1), v, logL, logV, vfast);
-        const float yv = a.y[o], xv = a.x[o];
-        const float z = yv - g * vs[v].invL;
-        const float mag = fabsf(z) - vs[v].thr;
-        const float xn = mag > 0.f ? copysignf(mag, z) : 0.f;
-        a.x[o] = xn;
-        a.y[o] = xn + beta * (xn - xv);
-      }
-      if (threadIdx.x == 0) s_t = tn;
-    }
-    // ---- objective 1/2 ||A x - b||^2 + lambda ||x||_1 and status
-    __syncthreads();
-    for (int v = threadIdx.x; v < V; v += kFThreads) vs[v].acc = 0.0;
-    pack_from(s, vs, a.x, logL, logV, vfast);
-    apply_T(s, vs, logL, logV, vfast, 0, a.tw, a.tw2);
-    __syncthreads();
-    gather_rows<true>(rr, s, vs, a.b, logL, logV, vfast, true);
-    __syncthreads();
-    for (int v = threadIdx.x; v < V; v += kFThreads) vs[v].cap = 0.5 * vs[v].acc;  // reuse cap: data term
-    __syncthreads();
-    for (int v = threadIdx.x; v < V; v += kFThreads) vs[v].acc = 0.0;
-    __syncthreads();
-    for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
-      const int v = q >> logL;
-      const float xv = vs[v].valid ? a.x[vs[v].x_off + (q & (Nc - 1))] : 0.f;
-      vec_add(vs, v, fabs((double)xv));
-    }
-    __syncthreads();
-    for (int v = threadIdx.x; v < V; v += kFThreads) {
-      if (!vs[v].valid) continue;
-      const int ii = vs[v].inst;
-      const double obj = vs[v].cap + vs[v].lam * vs[v].acc;
-      if (a.rep_L) a.rep_L[ii] = vs[v].L;
-      if (a.rep_lambda) a.rep_lambda[ii] = vs[v].lam;
-      if (a.rep_obj) a.rep_obj[ii] = obj;
-      if (a.rep_status) a.rep_status[ii] = isfinite(obj) ? 0 : (int)FM_ERR_NUMERIC;
+    switch (G.logn) {
+      case 8: fista_group<8>(a, G, s, vs, &s_t); break;
+      case 9: fista_group<9>(a, G, s, vs, &s_t); break;
+      case 10: fista_group<10>(a, G, s, vs, &s_t); break;
+      case 11: fista_group<11>(a, G, s, vs, &s_t); break;
+      case 12: fista_group<12>(a, G, s, vs, &s_t); break;
+      case 13: fista_group<13>(a, G, s, vs, &s_t); break;
+      default: fista_group<14>(a, G, s, vs, &s_t); break;
     }
   }
 }
@@ -456,6 +457,7 @@ fm_status fm_batch_create(const fm_op* A, int64_t count, void* stream, fm_batch*
     while ((1LL << logn) < n) ++logn;
     h[i].spec = T->spec32;
     h[i].idx = P->idx;
+    h[i].inv = P->inv;
     h[i].b_off = brow;
     h[i].x_off = xcol;
     h[i].n = (int)n;
@@ -552,6 +554,7 @@ fm_status fm_fista(fm_batch B, const float* b, float* x, const fm_fista_params* 
                    void* stream) {
   clear_error();
   if (!B || !b || !x || !p) { set_error("null pointer"); return FM_ERR_INVALID_ARG; }
+  if ((uintptr_t)x % 8) { set_error("x must be 8-byte aligned"); return FM_ERR_INVALID_ARG; }
   if (p->iters < 0 || p->power_iters < 1 || !(p->safety > 0.0) || !(p->lambda_rel >= 0.0) ||
       (p->mode != 0 && p->mode != 1)) {
     set_error("bad FISTA parameters");
