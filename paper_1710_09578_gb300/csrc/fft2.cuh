@@ -95,6 +95,73 @@ __device__ __forceinline__ void p2_compute(C (&r)[EPT], int dir, const C* __rest
   }
 }
 
+// Two-pass twiddle W_N^(t n2) of element t of a vector (n2 = its column in the plan).
+template <typename T>
+__device__ __forceinline__ typename Cx<T>::t tw_direct(typename Cx<T>::t x, const typename Cx<T>::t* tab,
+                                                      int64_t mask, int conj, int t, const VecInfo& vi) {
+  if (!tab) return x;
+  typename Cx<T>::t w = tab[((int64_t)t * vi.tw_n2) & mask];
+  return cmul(x, conj ? cconj(w) : w);
+}
+
+// The same twiddle along a staged loop in which a thread keeps one vector and t advances by
+// a constant: w <- w * W^(dt n2) after each element (falls back to table reads otherwise).
+template <typename T>
+struct TwRec {
+  typedef typename Cx<T>::t C;
+  const C* tab;
+  int64_t mask;
+  int conj;
+  bool rec;
+  C w, ws;
+  __device__ __forceinline__ TwRec(const C* tab_, int64_t mask_, int conj_, const VecInfo* vinfo, bool one_vector,
+                                   int dt, int logv)
+      : tab(tab_), mask(mask_), conj(conj_), rec(tab_ && one_vector) {
+    if (rec) {
+      const VecInfo& vi = vinfo[threadIdx.x & ((1 << logv) - 1)];
+      const int t0 = threadIdx.x >> logv;
+      w = tab[((int64_t)t0 * vi.tw_n2) & mask];
+      ws = tab[((int64_t)dt * vi.tw_n2) & mask];
+      if (conj) {
+        w = cconj(w);
+        ws = cconj(ws);
+      }
+    }
+  }
+  __device__ __forceinline__ C apply(C x, int t, const VecInfo& vi) {
+    if (!tab) return x;
+    if (!rec) return tw_direct<T>(x, tab, mask, conj, t, vi);
+    x = cmul(x, w);
+    w = cmul(w, ws);
+    return x;
+  }
+};
+
+// Multiply the registers of a radix-2^LR layout (element t = j + k L/R of vector v) by the
+// two-pass twiddle W_N^(t * n2(v)) (conjugated if conj): two table reads per butterfly.
+template <typename C, int THREADS, int EPT, int LOGL, int LOGV, int LR>
+__device__ __forceinline__ void p2_twiddle(C (&r)[EPT], const C* __restrict__ tab, int64_t mask, int conj,
+                                           const VecInfo* vinfo) {
+  constexpr int R = 1 << LR;
+#pragma unroll
+  for (int q = 0; q < EPT / R; ++q) {
+    int j, v;
+    bfly2<THREADS, LOGL, LOGV, LR>(q, j, v);
+    const int64_t n2 = vinfo[v].tw_n2;
+    C w = tab[((int64_t)j * n2) & mask];
+    C ws = tab[(((int64_t)1 << (LOGL - LR)) * n2) & mask];
+    if (conj) {
+      w = cconj(w);
+      ws = cconj(ws);
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      r[q * R + k] = cmul(r[q * R + k], w);
+      if (k + 1 < R) w = cmul(w, ws);
+    }
+  }
+}
+
 template <typename C, int THREADS, int EPT, int LOGL, int LOGV, int P, bool INV>
 __device__ __forceinline__ void p2_run(C (&r)[EPT], C* s, int dir, const C* tw) {
   using S = Sched<LOGL>;
@@ -112,7 +179,9 @@ __device__ __forceinline__ void p2_run(C (&r)[EPT], C* s, int dir, const C* tw) 
   }
 }
 
-template <typename T, int LOGL, int THREADS, int EPT>
+// SIMPLE: no fused operation on either side (complex in and out, natural index, no map,
+// diagonal, scale or accumulation): loads and stores are a base plus a stride.
+template <typename T, int LOGL, int THREADS, int EPT, bool SIMPLE>
 __global__ void __launch_bounds__(THREADS) fft2_kernel(const __grid_constant__ FftArgs<T> a) {
   typedef typename Cx<T>::t C;
   constexpr int E = THREADS * EPT, LOGE = ilog2c(E), LOGV = LOGE - LOGL, V = 1 << LOGV;
@@ -152,19 +221,35 @@ __global__ void __launch_bounds__(THREADS) fft2_kernel(const __grid_constant__ F
   __syncthreads();
 
   // load, staged in the order that is contiguous in HBM
-  if (a.in_vcontig) {
+  if (SIMPLE) {
+    const C* in = reinterpret_cast<const C*>(a.in);
+    const int64_t ts = a.in_tstride;
+#pragma unroll 4
+    for (int i = 0; i < EPT; ++i) {
+      const int e = threadIdx.x + i * THREADS;
+      int t, v;
+      if (a.in_vcontig) { v = e & (V - 1); t = e >> LOGV; }
+      else { t = e & (L - 1); v = e >> LOGL; }
+      const int64_t off = vinfo[v].in_off;
+      s[sp2<LOGL, LOGV>(t, v)] = (off >= 0 && t < a.Lin) ? in[off + t * ts] : cmake((T)0, (T)0);
+    }
+  } else if (a.in_vcontig) {
+    // vectors fastest: with V <= THREADS each thread keeps one vector and t steps by
+    // THREADS / V, so the two-pass twiddle W^(t n2) follows a recurrence
+    TwRec<T> tw(a.pre_tw, a.tw_mask, a.pre_tw_conj, vinfo, V <= THREADS, THREADS >> LOGV, LOGV);
 #pragma unroll 4
     for (int i = 0; i < EPT; ++i) {
       const int e = threadIdx.x + i * THREADS;
       const int v = e & (V - 1), t = e >> LOGV;
-      s[sp2<LOGL, LOGV>(t, v)] = fft_load<T>(a, vinfo[v], t);
+      s[sp2<LOGL, LOGV>(t, v)] = tw.apply(fft_load<T>(a, vinfo[v], t), t, vinfo[v]);
     }
   } else {
 #pragma unroll 4
     for (int i = 0; i < EPT; ++i) {
       const int e = threadIdx.x + i * THREADS;
       const int t = e & (L - 1), v = e >> LOGL;
-      s[sp2<LOGL, LOGV>(t, v)] = fft_load<T>(a, vinfo[v], t);
+      s[sp2<LOGL, LOGV>(t, v)] = tw_direct<T>(fft_load<T>(a, vinfo[v], t), a.pre_tw, a.tw_mask, a.pre_tw_conj, t,
+                                               vinfo[v]);
     }
   }
   __syncthreads();
@@ -196,27 +281,37 @@ __global__ void __launch_bounds__(THREADS) fft2_kernel(const __grid_constant__ F
   if (a.conv) p2_write<C, THREADS, EPT, LOGL, LOGV, LR0, LOGL - LR0>(r, s);
   else p2_write<C, THREADS, EPT, LOGL, LOGV, LRL, LOGL - LRL>(r, s);
   __syncthreads();
-  if (a.out_vcontig) {
+  if (SIMPLE) {
+    C* out = reinterpret_cast<C*>(a.out);
+    const int64_t ts = a.out_tstride;
+#pragma unroll 4
+    for (int i = 0; i < EPT; ++i) {
+      const int e = threadIdx.x + i * THREADS;
+      int t, v;
+      if (a.out_vcontig) { v = e & (V - 1); t = e >> LOGV; }
+      else { t = e & (L - 1); v = e >> LOGL; }
+      const int64_t off = vinfo[v].out_off;
+      if (off >= 0 && t < a.Lout) out[off + t * ts] = s[sp2<LOGL, LOGV>(t, v)];
+    }
+  } else if (a.out_vcontig) {
+    TwRec<T> tw(a.post_tw, a.tw_mask, a.post_tw_conj, vinfo, V <= THREADS, THREADS >> LOGV, LOGV);
 #pragma unroll 4
     for (int i = 0; i < EPT; ++i) {
       const int e = threadIdx.x + i * THREADS;
       const int v = e & (V - 1), t = e >> LOGV;
-      fft_store<T>(a, vinfo[v], t, s[sp2<LOGL, LOGV>(t, v)]);
+      fft_store<T>(a, vinfo[v], t, tw.apply(s[sp2<LOGL, LOGV>(t, v)], t, vinfo[v]));
     }
   } else {
 #pragma unroll 4
     for (int i = 0; i < EPT; ++i) {
       const int e = threadIdx.x + i * THREADS;
       const int t = e & (L - 1), v = e >> LOGL;
-      fft_store<T>(a, vinfo[v], t, s[sp2<LOGL, LOGV>(t, v)]);
+      fft_store<T>(a, vinfo[v], t,
+                   tw_direct<T>(s[sp2<LOGL, LOGV>(t, v)], a.post_tw, a.tw_mask, a.post_tw_conj, t, vinfo[v]));
     }
   }
 }
 
-// Tile shape: E = THREADS * EPT elements.  Contiguous vectors use the smallest tile that
-// holds one vector (at least 4096 elements); strided views (vectors along the inner index)
-// use E >= 16 L when possible, so that a tile row is 16 vectors wide (128-byte HBM rows,
-// conflict-free shared-memory layout).
 template <int LOGL, bool WIDE> struct TileCfg {
   static constexpr int LOGE = WIDE ? (LOGL + 4 > 14 ? 14 : (LOGL + 4 < 12 ? 12 : LOGL + 4))
                                    : (LOGL < 12 ? 12 : LOGL);
@@ -242,14 +337,17 @@ fm_status fft2_launch_cfg(FftArgs<T> a, cudaStream_t st) {
   a.in_vcontig = (a.inner > 1 || a.in_ostride == 1) ? 1 : 0;
   a.out_vcontig = (a.inner > 1 || a.out_ostride == 1) ? 1 : 0;
   const size_t smem = fft_vinfo_offset<C>(E) + (size_t)V * sizeof(VecInfo);
-  auto kern = fft2_kernel<T, LOGL, THREADS, EPT>;
+  const bool simple = a.in_mode == IO_C && a.out_mode == IO_C && !a.pre_map && !a.pre_dc && !a.pre_dr &&
+                      !a.pre_tw && !a.post_tw && !a.post_dc && !a.post_dr && !a.post_map && a.scale == (T)1 &&
+                      !a.beta && a.in_fmul == 1 && a.in_fmod == 1 && a.out_fmul == 1 && a.out_fmod == 1;
+  auto kern = simple ? fft2_kernel<T, LOGL, THREADS, EPT, true> : fft2_kernel<T, LOGL, THREADS, EPT, false>;
   int dev = 0;
   cudaGetDevice(&dev);
-  static std::atomic<unsigned long long> attr_bytes[32];
-  if (dev < 32 && attr_bytes[dev].load() < smem) {
+  static std::atomic<unsigned long long> attr_bytes[2][32];
+  if (dev < 32 && attr_bytes[simple][dev].load() < smem) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) { set_error("fft smem attribute: %s", cudaGetErrorString(e)); return FM_ERR_CUDA; }
-    attr_bytes[dev].store(smem);
+    attr_bytes[simple][dev].store(smem);
   }
   kern<<<(unsigned)tiles, THREADS, smem, st>>>(a);
   return after_launch("fft2_kernel");

@@ -66,10 +66,6 @@ __device__ __forceinline__ typename Cx<T>::t fft_load(const FftArgs<T>& a, const
   } else if (a.pre_dr) {
     x = cscale(x, a.pre_dr[n]);
   }
-  if (a.pre_tw) {
-    C w = a.pre_tw[((int64_t)t * vi.tw_n2) & a.tw_mask];
-    x = cmul(x, a.pre_tw_conj ? cconj(w) : w);
-  }
   return x;
 }
 
@@ -77,10 +73,6 @@ template <typename T>
 __device__ __forceinline__ void fft_store(const FftArgs<T>& a, const VecInfo& vi, int t, typename Cx<T>::t x) {
   typedef typename Cx<T>::t C;
   if (vi.out_off < 0) return;
-  if (a.post_tw) {
-    C w = a.post_tw[((int64_t)t * vi.tw_n2) & a.tw_mask];
-    x = cmul(x, a.post_tw_conj ? cconj(w) : w);
-  }
   const int64_t n = (int64_t)t * a.out_fmul + vi.out_n2;
   if (n >= a.Lout) return;
   if (a.post_dc) {
