@@ -104,6 +104,23 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def job_throughput(t_local: float, units_local: float, pg=None, device=None):
+    """Whole-job throughput of independent replicas: units of all ranks / the slowest rank's time.
+
+    Every rank passes its own timed seconds and processed units; with a process group the
+    time is max-reduced and the units sum-reduced (replicas exchange nothing else).
+    """
+    if pg is None:
+        return units_local / t_local, t_local
+    import torch
+    tt = torch.tensor([t_local, units_local], dtype=torch.float64, device=device)
+    tmax = tt[:1].clone()
+    pg.all_reduce(tmax, op=pg.ReduceOp.MAX)
+    units = tt[1:].clone()
+    pg.all_reduce(units, op=pg.ReduceOp.SUM)
+    return units.item() / tmax.item(), tmax.item()
+
+
 def dist_init():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -240,12 +257,9 @@ def main():
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
-    t_total = e0.elapsed_time(e1) / 1e3
-    if pg:
-        tt = torch.tensor([t_total], device=dev, dtype=torch.float64)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        t_total = tt.item()
-    value = world * STEP_BYTES * args.steps / t_total / 1e9
+    t_local = e0.elapsed_time(e1) / 1e3
+    rate, t_total = job_throughput(t_local, float(STEP_BYTES) * args.steps, pg, dev)
+    value = rate / 1e9
 
     # ---- roofline of the dominant kernel: back-to-back forward launches on rotating sets
     nl = 400
