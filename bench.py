@@ -339,6 +339,14 @@ def measure_rows(fm, torch, dev, stream, flush, xi, cpu_sample=True):
     rows["hadamard_int8_fwd"] = {"GB/s": _gbs_loop(lambda: Ai.forward(Xi, out=Yi), N * NCOLS * 5, 200, flush,
                                                    stream, torch)}
     del Xi, Yi
+    # BF16 tensor-core Hadamard (FP32 in and out, BF16 products with FP32 accumulation) and its
+    # split hi + lo form
+    Xf = torch.from_numpy(I.hadamard_block()[0]).to(dev)
+    Yf = torch.empty_like(Xf)
+    for name, mode in (("hadamard_bf16_fwd", fm.FM_HAD_BF16), ("hadamard_bf16x2_fwd", fm.FM_HAD_BF16X2)):
+        Ab = fm.hadamard(LOG2N, mode)
+        rows[name] = {"GB/s": _gbs_loop(lambda: Ab.forward(Xf, out=Yf), APPLY_BYTES, 200, flush, stream, torch)}
+    del Xf, Yf
     # compressed-sensing operator Phi = P Diag(d) C, N = 2^18, 64 complex64 columns
     c, d, idx, X, Yc, _ = I.cs_operator()
     n = len(c)

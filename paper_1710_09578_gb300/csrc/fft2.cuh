@@ -100,7 +100,7 @@ template <typename T>
 __device__ __forceinline__ typename Cx<T>::t tw_direct(typename Cx<T>::t x, const typename Cx<T>::t* tab,
                                                       int64_t mask, int conj, int t, const VecInfo& vi) {
   if (!tab) return x;
-  typename Cx<T>::t w = tab[((int64_t)t * vi.tw_n2) & mask];
+  typename Cx<T>::t w = gld(tab + (((int64_t)t * vi.tw_n2) & mask));
   return cmul(x, conj ? cconj(w) : w);
 }
 
@@ -120,8 +120,8 @@ struct TwRec {
     if (rec) {
       const VecInfo& vi = vinfo[threadIdx.x & ((1 << logv) - 1)];
       const int t0 = threadIdx.x >> logv;
-      w = tab[((int64_t)t0 * vi.tw_n2) & mask];
-      ws = tab[((int64_t)dt * vi.tw_n2) & mask];
+      w = gld(tab + (((int64_t)t0 * vi.tw_n2) & mask));
+      ws = gld(tab + (((int64_t)dt * vi.tw_n2) & mask));
       if (conj) {
         w = cconj(w);
         ws = cconj(ws);
@@ -136,31 +136,6 @@ struct TwRec {
     return x;
   }
 };
-
-// Multiply the registers of a radix-2^LR layout (element t = j + k L/R of vector v) by the
-// two-pass twiddle W_N^(t * n2(v)) (conjugated if conj): two table reads per butterfly.
-template <typename C, int THREADS, int EPT, int LOGL, int LOGV, int LR>
-__device__ __forceinline__ void p2_twiddle(C (&r)[EPT], const C* __restrict__ tab, int64_t mask, int conj,
-                                           const VecInfo* vinfo) {
-  constexpr int R = 1 << LR;
-#pragma unroll
-  for (int q = 0; q < EPT / R; ++q) {
-    int j, v;
-    bfly2<THREADS, LOGL, LOGV, LR>(q, j, v);
-    const int64_t n2 = vinfo[v].tw_n2;
-    C w = tab[((int64_t)j * n2) & mask];
-    C ws = tab[(((int64_t)1 << (LOGL - LR)) * n2) & mask];
-    if (conj) {
-      w = cconj(w);
-      ws = cconj(ws);
-    }
-#pragma unroll
-    for (int k = 0; k < R; ++k) {
-      r[q * R + k] = cmul(r[q * R + k], w);
-      if (k + 1 < R) w = cmul(w, ws);
-    }
-  }
-}
 
 template <typename C, int THREADS, int EPT, int LOGL, int LOGV, int P, bool INV>
 __device__ __forceinline__ void p2_run(C (&r)[EPT], C* s, int dir, const C* tw) {
@@ -181,8 +156,15 @@ __device__ __forceinline__ void p2_run(C (&r)[EPT], C* s, int dir, const C* tw) 
 
 // SIMPLE: no fused operation on either side (complex in and out, natural index, no map,
 // diagonal, scale or accumulation): loads and stores are a base plus a stride.
+// Resident CTAs per SM the register allocation is held to, for FP32 tiles: 3 x 256 threads
+// (24 warps per SM), 2 x 512 x 16; the 512 x 32 and FP64 tiles need their registers.
+template <typename T, int THREADS, int EPT>
+__host__ __device__ constexpr int fft2_min_blocks() {
+  return sizeof(T) != 4 ? 1 : (THREADS <= 256 ? 3 : (EPT <= 16 ? 2 : 1));
+}
+
 template <typename T, int LOGL, int THREADS, int EPT, bool SIMPLE>
-__global__ void __launch_bounds__(THREADS) fft2_kernel(const __grid_constant__ FftArgs<T> a) {
+__global__ void __launch_bounds__(THREADS, fft2_min_blocks<T, THREADS, EPT>()) fft2_kernel(const __grid_constant__ FftArgs<T> a) {
   typedef typename Cx<T>::t C;
   constexpr int E = THREADS * EPT, LOGE = ilog2c(E), LOGV = LOGE - LOGL, V = 1 << LOGV;
   constexpr int L = 1 << LOGL;
@@ -220,41 +202,61 @@ __global__ void __launch_bounds__(THREADS) fft2_kernel(const __grid_constant__ F
   }
   __syncthreads();
 
-  // load, staged in the order that is contiguous in HBM
+  // load: every element of this thread first (all loads in flight together), then the
+  // shared-memory stores, in the order that is contiguous in HBM
+  C r[EPT];
   if (SIMPLE) {
     const C* in = reinterpret_cast<const C*>(a.in);
     const int64_t ts = a.in_tstride;
-#pragma unroll 4
+#pragma unroll
     for (int i = 0; i < EPT; ++i) {
       const int e = threadIdx.x + i * THREADS;
       int t, v;
       if (a.in_vcontig) { v = e & (V - 1); t = e >> LOGV; }
       else { t = e & (L - 1); v = e >> LOGL; }
       const int64_t off = vinfo[v].in_off;
-      s[sp2<LOGL, LOGV>(t, v)] = (off >= 0 && t < a.Lin) ? in[off + t * ts] : cmake((T)0, (T)0);
+      r[i] = (off >= 0 && t < a.Lin) ? gld(in + off + t * ts) : cmake((T)0, (T)0);
+    }
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) {
+      const int e = threadIdx.x + i * THREADS;
+      int t, v;
+      if (a.in_vcontig) { v = e & (V - 1); t = e >> LOGV; }
+      else { t = e & (L - 1); v = e >> LOGL; }
+      s[sp2<LOGL, LOGV>(t, v)] = r[i];
     }
   } else if (a.in_vcontig) {
     // vectors fastest: with V <= THREADS each thread keeps one vector and t steps by
     // THREADS / V, so the two-pass twiddle W^(t n2) follows a recurrence
-    TwRec<T> tw(a.pre_tw, a.tw_mask, a.pre_tw_conj, vinfo, V <= THREADS, THREADS >> LOGV, LOGV);
-#pragma unroll 4
+#pragma unroll
     for (int i = 0; i < EPT; ++i) {
       const int e = threadIdx.x + i * THREADS;
       const int v = e & (V - 1), t = e >> LOGV;
-      s[sp2<LOGL, LOGV>(t, v)] = tw.apply(fft_load<T>(a, vinfo[v], t), t, vinfo[v]);
+      r[i] = fft_load<T>(a, vinfo[v], t);
+    }
+    TwRec<T> tw(a.pre_tw, a.tw_mask, a.pre_tw_conj, vinfo, V <= THREADS, THREADS >> LOGV, LOGV);
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) {
+      const int e = threadIdx.x + i * THREADS;
+      const int v = e & (V - 1), t = e >> LOGV;
+      s[sp2<LOGL, LOGV>(t, v)] = tw.apply(r[i], t, vinfo[v]);
     }
   } else {
-#pragma unroll 4
+#pragma unroll
     for (int i = 0; i < EPT; ++i) {
       const int e = threadIdx.x + i * THREADS;
       const int t = e & (L - 1), v = e >> LOGL;
-      s[sp2<LOGL, LOGV>(t, v)] = tw_direct<T>(fft_load<T>(a, vinfo[v], t), a.pre_tw, a.tw_mask, a.pre_tw_conj, t,
-                                               vinfo[v]);
+      r[i] = fft_load<T>(a, vinfo[v], t);
+    }
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) {
+      const int e = threadIdx.x + i * THREADS;
+      const int t = e & (L - 1), v = e >> LOGL;
+      s[sp2<LOGL, LOGV>(t, v)] = tw_direct<T>(r[i], a.pre_tw, a.tw_mask, a.pre_tw_conj, t, vinfo[v]);
     }
   }
   __syncthreads();
 
-  C r[EPT];
   constexpr int LR0 = S::lr(0);
   constexpr int LRL = S::lr(S::NR - 1);
   p2_read<C, THREADS, EPT, LOGL, LOGV, LR0>(r, s);
@@ -269,7 +271,7 @@ __global__ void __launch_bounds__(THREADS) fft2_kernel(const __grid_constant__ F
       const C* sp = a.spec + vinfo[v].soff + j;
 #pragma unroll
       for (int k = 0; k < R; ++k) {
-        C w = sp[k << (LOGL - LRL)];
+        C w = gld(sp + (k << (LOGL - LRL)));
         r[q * R + k] = cmul(r[q * R + k], a.spec_conj ? cconj(w) : w);
       }
     }
@@ -284,30 +286,49 @@ __global__ void __launch_bounds__(THREADS) fft2_kernel(const __grid_constant__ F
   if (SIMPLE) {
     C* out = reinterpret_cast<C*>(a.out);
     const int64_t ts = a.out_tstride;
-#pragma unroll 4
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) {
+      const int e = threadIdx.x + i * THREADS;
+      int t, v;
+      if (a.out_vcontig) { v = e & (V - 1); t = e >> LOGV; }
+      else { t = e & (L - 1); v = e >> LOGL; }
+      r[i] = s[sp2<LOGL, LOGV>(t, v)];
+    }
+#pragma unroll
     for (int i = 0; i < EPT; ++i) {
       const int e = threadIdx.x + i * THREADS;
       int t, v;
       if (a.out_vcontig) { v = e & (V - 1); t = e >> LOGV; }
       else { t = e & (L - 1); v = e >> LOGL; }
       const int64_t off = vinfo[v].out_off;
-      if (off >= 0 && t < a.Lout) out[off + t * ts] = s[sp2<LOGL, LOGV>(t, v)];
-    }
-  } else if (a.out_vcontig) {
-    TwRec<T> tw(a.post_tw, a.tw_mask, a.post_tw_conj, vinfo, V <= THREADS, THREADS >> LOGV, LOGV);
-#pragma unroll 4
-    for (int i = 0; i < EPT; ++i) {
-      const int e = threadIdx.x + i * THREADS;
-      const int v = e & (V - 1), t = e >> LOGV;
-      fft_store<T>(a, vinfo[v], t, tw.apply(s[sp2<LOGL, LOGV>(t, v)], t, vinfo[v]));
+      if (off >= 0 && t < a.Lout) gst(out + off + t * ts, r[i]);
     }
   } else {
-#pragma unroll 4
-    for (int i = 0; i < EPT; ++i) {
-      const int e = threadIdx.x + i * THREADS;
-      const int t = e & (L - 1), v = e >> LOGL;
-      fft_store<T>(a, vinfo[v], t,
-                   tw_direct<T>(s[sp2<LOGL, LOGV>(t, v)], a.post_tw, a.tw_mask, a.post_tw_conj, t, vinfo[v]));
+    // two phases in groups of 8 elements: the loads of the fused post operations (diagonal,
+    // row map) of a group first, then its stores
+    constexpr int G = EPT < 8 ? EPT : 8;
+    TwRec<T> tw(a.post_tw, a.tw_mask, a.post_tw_conj, vinfo, a.out_vcontig && V <= THREADS, THREADS >> LOGV, LOGV);
+#pragma unroll
+    for (int g = 0; g < EPT; g += G) {
+      int dst[G];
+#pragma unroll
+      for (int k = 0; k < G; ++k) {
+        const int e = threadIdx.x + (g + k) * THREADS;
+        int t, v;
+        if (a.out_vcontig) { v = e & (V - 1); t = e >> LOGV; }
+        else { t = e & (L - 1); v = e >> LOGL; }
+        C x = s[sp2<LOGL, LOGV>(t, v)];
+        x = a.out_vcontig ? tw.apply(x, t, vinfo[v])
+                          : tw_direct<T>(x, a.post_tw, a.tw_mask, a.post_tw_conj, t, vinfo[v]);
+        dst[k] = fft_store_prep<T>(a, vinfo[v], t, x);
+        r[g + k] = x;
+      }
+#pragma unroll
+      for (int k = 0; k < G; ++k) {
+        const int e = threadIdx.x + (g + k) * THREADS;
+        const int v = a.out_vcontig ? (e & (V - 1)) : (e >> LOGL);
+        fft_store_commit<T>(a, vinfo[v], dst[k], r[g + k]);
+      }
     }
   }
 }

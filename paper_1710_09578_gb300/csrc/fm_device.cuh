@@ -60,6 +60,49 @@ template <typename C> __device__ __forceinline__ void dft8(C* a, int dir) {
   a[7] = csub(e[3], o3);
 }
 
+// Global-space loads and stores.  With the state space explicit (rather than a generic
+// address that might point into shared memory) the instruction scheduler may move a load
+// ahead of unrelated shared-memory stores, so a thread can have all the loads of a tile in
+// flight at once.  The loads are volatile so that the compiler never executes one
+// speculatively, outside the bounds check that guards it.
+__device__ __forceinline__ float gld(const float* p) {
+  float r;
+  asm volatile("ld.global.f32 %0, [%1];" : "=f"(r) : "l"(p));
+  return r;
+}
+__device__ __forceinline__ double gld(const double* p) {
+  double r;
+  asm volatile("ld.global.f64 %0, [%1];" : "=d"(r) : "l"(p));
+  return r;
+}
+__device__ __forceinline__ float2 gld(const float2* p) {
+  float2 r;
+  asm volatile("ld.global.v2.f32 {%0, %1}, [%2];" : "=f"(r.x), "=f"(r.y) : "l"(p));
+  return r;
+}
+__device__ __forceinline__ double2 gld(const double2* p) {
+  double2 r;
+  asm volatile("ld.global.v2.f64 {%0, %1}, [%2];" : "=d"(r.x), "=d"(r.y) : "l"(p));
+  return r;
+}
+__device__ __forceinline__ int gld(const int32_t* p) {
+  int r;
+  asm volatile("ld.global.s32 %0, [%1];" : "=r"(r) : "l"(p));
+  return r;
+}
+__device__ __forceinline__ void gst(float* p, float v) {
+  asm volatile("st.global.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+__device__ __forceinline__ void gst(double* p, double v) {
+  asm volatile("st.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+__device__ __forceinline__ void gst(float2* p, float2 v) {
+  asm volatile("st.global.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ void gst(double2* p, double2 v) {
+  asm volatile("st.global.v2.f64 [%0], {%1, %2};" ::"l"(p), "d"(v.x), "d"(v.y) : "memory");
+}
+
 // Shared-memory index with one pad slot every 16 elements (breaks power-of-two strides).
 __device__ __forceinline__ int spad(int lin) { return lin + (lin >> 4); }
 
