@@ -1,13 +1,21 @@
 // Tile FFT kernel with the transform length fixed at compile time.
 //
-// Same algorithm and the same launch descriptor (FftArgs) as the runtime-length engine in
-// fft_impl.cuh -- V vectors of length L per CTA in shared memory, radix-8/4/2 Stockham
-// passes with the elements of each butterfly in registers, the spectrum product of a
-// circulant between the last forward and the first inverse pass -- but with L a template
-// parameter the radix schedule, the thread-to-butterfly mapping and every in-tile index
-// are compile-time constants, so the passes unroll completely and the shared-memory
-// addresses of a butterfly reduce to one base plus constant strides.  Loads and stores
-// still go through the per-vector table and the fused pre/post operations of FftArgs.
+// V vectors of length L per CTA, radix-8/4/2 Stockham passes with the elements of each
+// butterfly in registers (the DFT of Eq. (1) by the butterfly factorisation of Sec. 1) and
+// the spectrum product of a circulant (Eq. (5)) in registers between the last forward and
+// the first inverse pass.  With L a template parameter the radix schedule, the
+// thread-to-butterfly mapping and every in-tile index are compile-time constants, so the
+// passes unroll completely.
+//
+// The first pass reads its butterfly inputs (elements j + k L/R) straight from HBM and the
+// last pass writes its outputs (natural order, j + k L/R) straight to HBM; shared memory
+// only carries the exchanges between passes.  The thread-to-butterfly mapping follows the
+// layout in HBM: VF (vectors contiguous, a strided axis) gives consecutive threads
+// consecutive vectors, otherwise consecutive threads take consecutive elements of a
+// vector, so each warp access is a few full 32-byte sectors either way.  A thread issues
+// all of its loads before the first shared-memory store.  Loads and stores go through the
+// per-vector table and the fused pre/post operations of FftArgs (Diag, row selection,
+// zero-padding and truncation, two-pass twiddles, scale, accumulation).
 #pragma once
 #include "fft_impl.cuh"
 
@@ -26,16 +34,17 @@ struct Sched {
   }
 };
 
-template <int LOGL, int LOGV>
+// Shared-memory word of element t of tile vector v (VF: vectors fastest), one pad slot
+// every 16 words.
+template <bool VF, int LOGL, int LOGV>
 __device__ __forceinline__ int sp2(int t, int v) {
-  constexpr bool VF = (1 << LOGV) >= 16;
   const int lin = VF ? ((t << LOGV) + v) : ((v << LOGL) + t);
   return lin + (lin >> 4);
 }
 
-template <int THREADS, int LOGL, int LOGV, int LR>
+// Butterfly q of this thread in a radix-2^LR pass: vector v, index j in [0, L/R).
+template <bool VF, int THREADS, int LOGL, int LOGV, int LR>
 __device__ __forceinline__ void bfly2(int q, int& j, int& v) {
-  constexpr bool VF = (1 << LOGV) >= 16;
   const int b = threadIdx.x + q * THREADS;
   if (VF) {
     v = b & ((1 << LOGV) - 1);
@@ -46,41 +55,41 @@ __device__ __forceinline__ void bfly2(int q, int& j, int& v) {
   }
 }
 
-template <typename C, int THREADS, int EPT, int LOGL, int LOGV, int LR>
+template <typename C, bool VF, int THREADS, int EPT, int LOGL, int LOGV, int LR>
 __device__ __forceinline__ void p2_read(C (&r)[EPT], const C* s) {
   constexpr int R = 1 << LR;
 #pragma unroll
   for (int q = 0; q < EPT / R; ++q) {
     int j, v;
-    bfly2<THREADS, LOGL, LOGV, LR>(q, j, v);
+    bfly2<VF, THREADS, LOGL, LOGV, LR>(q, j, v);
 #pragma unroll
-    for (int k = 0; k < R; ++k) r[q * R + k] = s[sp2<LOGL, LOGV>(j + (k << (LOGL - LR)), v)];
+    for (int k = 0; k < R; ++k) r[q * R + k] = s[sp2<VF, LOGL, LOGV>(j + (k << (LOGL - LR)), v)];
   }
 }
 
 // outputs of a radix-2^LR pass to (j / Ns) Ns R + j % Ns + k Ns (natural order when Ns R = L)
-template <typename C, int THREADS, int EPT, int LOGL, int LOGV, int LR, int LOGNS>
+template <typename C, bool VF, int THREADS, int EPT, int LOGL, int LOGV, int LR, int LOGNS>
 __device__ __forceinline__ void p2_write(const C (&r)[EPT], C* s) {
   constexpr int R = 1 << LR;
 #pragma unroll
   for (int q = 0; q < EPT / R; ++q) {
     int j, v;
-    bfly2<THREADS, LOGL, LOGV, LR>(q, j, v);
+    bfly2<VF, THREADS, LOGL, LOGV, LR>(q, j, v);
     const int base = ((j >> LOGNS) << (LOGNS + LR)) + (j & ((1 << LOGNS) - 1));
 #pragma unroll
-    for (int k = 0; k < R; ++k) s[sp2<LOGL, LOGV>(base + (k << LOGNS), v)] = r[q * R + k];
+    for (int k = 0; k < R; ++k) s[sp2<VF, LOGL, LOGV>(base + (k << LOGNS), v)] = r[q * R + k];
   }
 }
 
-template <typename C, int THREADS, int EPT, int LOGL, int LOGV, int LR, int LOGNS>
+template <typename C, bool VF, int THREADS, int EPT, int LOGL, int LOGV, int LR, int LOGNS>
 __device__ __forceinline__ void p2_compute(C (&r)[EPT], int dir, const C* __restrict__ tw) {
   constexpr int R = 1 << LR;
 #pragma unroll
   for (int q = 0; q < EPT / R; ++q) {
     if (LOGNS > 0) {
       int j, v;
-      bfly2<THREADS, LOGL, LOGV, LR>(q, j, v);
-      C w = tw[(j & ((1 << LOGNS) - 1)) << (kTwLog - LOGNS - LR)];
+      bfly2<VF, THREADS, LOGL, LOGV, LR>(q, j, v);
+      C w = gld(tw + ((j & ((1 << LOGNS) - 1)) << (kTwLog - LOGNS - LR)));
       if (dir > 0) w = cconj(w);
       C wk = w;
 #pragma unroll
@@ -95,83 +104,136 @@ __device__ __forceinline__ void p2_compute(C (&r)[EPT], int dir, const C* __rest
   }
 }
 
-// Two-pass twiddle W_N^(t n2) of element t of a vector (n2 = its column in the plan).
-template <typename T>
-__device__ __forceinline__ typename Cx<T>::t tw_direct(typename Cx<T>::t x, const typename Cx<T>::t* tab,
-                                                      int64_t mask, int conj, int t, const VecInfo& vi) {
-  if (!tab) return x;
-  typename Cx<T>::t w = gld(tab + (((int64_t)t * vi.tw_n2) & mask));
-  return cmul(x, conj ? cconj(w) : w);
-}
-
-// The same twiddle along a staged loop in which a thread keeps one vector and t advances by
-// a constant: w <- w * W^(dt n2) after each element (falls back to table reads otherwise).
-template <typename T>
-struct TwRec {
-  typedef typename Cx<T>::t C;
-  const C* tab;
-  int64_t mask;
-  int conj;
-  bool rec;
-  C w, ws;
-  __device__ __forceinline__ TwRec(const C* tab_, int64_t mask_, int conj_, const VecInfo* vinfo, bool one_vector,
-                                   int dt, int logv)
-      : tab(tab_), mask(mask_), conj(conj_), rec(tab_ && one_vector) {
-    if (rec) {
-      const VecInfo& vi = vinfo[threadIdx.x & ((1 << logv) - 1)];
-      const int t0 = threadIdx.x >> logv;
-      w = gld(tab + (((int64_t)t0 * vi.tw_n2) & mask));
-      ws = gld(tab + (((int64_t)dt * vi.tw_n2) & mask));
-      if (conj) {
-        w = cconj(w);
-        ws = cconj(ws);
-      }
-    }
-  }
-  __device__ __forceinline__ C apply(C x, int t, const VecInfo& vi) {
-    if (!tab) return x;
-    if (!rec) return tw_direct<T>(x, tab, mask, conj, t, vi);
-    x = cmul(x, w);
-    w = cmul(w, ws);
-    return x;
-  }
-};
-
-template <typename C, int THREADS, int EPT, int LOGL, int LOGV, int P, bool INV>
+template <typename C, bool VF, int THREADS, int EPT, int LOGL, int LOGV, int P, bool INV>
 __device__ __forceinline__ void p2_run(C (&r)[EPT], C* s, int dir, const C* tw) {
   using S = Sched<LOGL>;
   if constexpr (P < S::NR) {
     constexpr int LR = INV ? S::lr(S::NR - 1 - P) : S::lr(P);
     constexpr int LOGNS = INV ? S::ns_inv(P) : 3 * P;
-    if constexpr (P > 0) p2_read<C, THREADS, EPT, LOGL, LOGV, LR>(r, s);
-    p2_compute<C, THREADS, EPT, LOGL, LOGV, LR, LOGNS>(r, dir, tw);
+    if constexpr (P > 0) p2_read<C, VF, THREADS, EPT, LOGL, LOGV, LR>(r, s);
+    p2_compute<C, VF, THREADS, EPT, LOGL, LOGV, LR, LOGNS>(r, dir, tw);
     if constexpr (P + 1 < S::NR) {
       __syncthreads();
-      p2_write<C, THREADS, EPT, LOGL, LOGV, LR, LOGNS>(r, s);
+      p2_write<C, VF, THREADS, EPT, LOGL, LOGV, LR, LOGNS>(r, s);
       __syncthreads();
     }
-    p2_run<C, THREADS, EPT, LOGL, LOGV, P + 1, INV>(r, s, dir, tw);
+    p2_run<C, VF, THREADS, EPT, LOGL, LOGV, P + 1, INV>(r, s, dir, tw);
   }
 }
 
-// SIMPLE: no fused operation on either side (complex in and out, natural index, no map,
-// diagonal, scale or accumulation): loads and stores are a base plus a stride.
+// Two-pass twiddle W_N^(t n2) on the R elements t = j + k M of a butterfly (n2 = the
+// vector's column in the plan): one table read for j, one for the step M, then a recurrence.
+template <typename T, int R>
+__device__ __forceinline__ void tw_bfly(typename Cx<T>::t* x, const typename Cx<T>::t* tab, int64_t mask, int conj,
+                                        int j, int M, int64_t n2) {
+  typedef typename Cx<T>::t C;
+  C w = gld(tab + (((int64_t)j * n2) & mask));
+  C ws = gld(tab + (((int64_t)M * n2) & mask));
+  if (conj) {
+    w = cconj(w);
+    ws = cconj(ws);
+  }
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    x[k] = cmul(x[k], w);
+    if (k + 1 < R) w = cmul(w, ws);
+  }
+}
+
+// Inputs of the first pass straight from HBM: element j + k L/R of vector v into register
+// q R + k of butterfly q, every load issued before any is used.
+template <typename T, bool VF, bool SIMPLE, int THREADS, int EPT, int LOGL, int LOGV, int LR>
+__device__ __forceinline__ void load_first(typename Cx<T>::t (&r)[EPT], const FftArgs<T>& a,
+                                           const VecInfo* vinfo) {
+  typedef typename Cx<T>::t C;
+  constexpr int R = 1 << LR, M = 1 << (LOGL - LR);
+#pragma unroll
+  for (int q = 0; q < EPT / R; ++q) {
+    int j, v;
+    bfly2<VF, THREADS, LOGL, LOGV, LR>(q, j, v);
+    const VecInfo& vi = vinfo[v];
+    if (SIMPLE) {
+      // unit stride: constant offsets from one base; otherwise one base and a step
+      const bool unit = a.in_tstride == 1;
+      const int64_t step = unit ? M : (int64_t)M * a.in_tstride;
+      const C* in = reinterpret_cast<const C*>(a.in) + vi.in_off + (unit ? j : (int64_t)j * a.in_tstride);
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        const bool ok = vi.in_off >= 0 && j + k * M < a.Lin;
+        r[q * R + k] = ok ? gld(unit ? in + k * M : in + k * step) : cmake((T)0, (T)0);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < R; ++k) r[q * R + k] = fft_load<T>(a, vi, j + k * M);
+    }
+  }
+  if (!SIMPLE && a.pre_tw) {
+#pragma unroll
+    for (int q = 0; q < EPT / R; ++q) {
+      int j, v;
+      bfly2<VF, THREADS, LOGL, LOGV, LR>(q, j, v);
+      tw_bfly<T, R>(&r[q * R], a.pre_tw, a.tw_mask, a.pre_tw_conj, j, M, vinfo[v].tw_n2);
+    }
+  }
+}
+
+// Outputs of the last pass (natural order, element j + k L/R in register q R + k) straight
+// to HBM; with fused post operations the loads they need for a butterfly come first.
+template <typename T, bool VF, bool SIMPLE, int THREADS, int EPT, int LOGL, int LOGV, int LR>
+__device__ __forceinline__ void store_last(typename Cx<T>::t (&r)[EPT], const FftArgs<T>& a,
+                                           const VecInfo* vinfo) {
+  typedef typename Cx<T>::t C;
+  constexpr int R = 1 << LR, M = 1 << (LOGL - LR);
+#pragma unroll
+  for (int q = 0; q < EPT / R; ++q) {
+    int j, v;
+    bfly2<VF, THREADS, LOGL, LOGV, LR>(q, j, v);
+    const VecInfo& vi = vinfo[v];
+    if (SIMPLE) {
+      const bool unit = a.out_tstride == 1;
+      const int64_t step = unit ? M : (int64_t)M * a.out_tstride;
+      C* out = reinterpret_cast<C*>(a.out) + vi.out_off + (unit ? j : (int64_t)j * a.out_tstride);
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        if (vi.out_off >= 0 && j + k * M < a.Lout) gst(unit ? out + k * M : out + k * step, r[q * R + k]);
+      }
+    } else {
+      if (a.post_tw) tw_bfly<T, R>(&r[q * R], a.post_tw, a.tw_mask, a.post_tw_conj, j, M, vi.tw_n2);
+      int dst[R];
+#pragma unroll
+      for (int k = 0; k < R; ++k) dst[k] = fft_store_prep<T>(a, vi, j + k * M, r[q * R + k]);
+#pragma unroll
+      for (int k = 0; k < R; ++k) fft_store_commit<T>(a, vi, dst[k], r[q * R + k]);
+    }
+  }
+}
+
 // Resident CTAs per SM the register allocation is held to, for FP32 tiles: 3 x 256 threads
 // (24 warps per SM), 2 x 512 x 16; the 512 x 32 and FP64 tiles need their registers.
-template <typename T, int THREADS, int EPT>
+template <typename T, int THREADS, int EPT, bool CONV>
 __host__ __device__ constexpr int fft2_min_blocks() {
   return sizeof(T) != 4 ? 1 : (THREADS <= 256 ? 3 : (EPT <= 16 ? 2 : 1));
 }
 
-template <typename T, int LOGL, int THREADS, int EPT, bool SIMPLE>
-__global__ void __launch_bounds__(THREADS, fft2_min_blocks<T, THREADS, EPT>()) fft2_kernel(const __grid_constant__ FftArgs<T> a) {
+// The exchange buffer (none when a single radix pass does the whole transform in
+// registers), then the per-vector table.
+template <typename C, int LOGL>
+__host__ __device__ constexpr size_t fft2_vinfo_offset(int E) {
+  return Sched<LOGL>::NR > 1 ? fft_vinfo_offset<C>(E) : 0;
+}
+
+// SIMPLE: no fused operation on either side (complex in and out, natural index, no map,
+// diagonal, twiddle, scale or accumulation): loads and stores are a base plus a stride.
+// CONV: transform, spectrum product, inverse transform (circulant and Toeplitz products).
+template <typename T, int LOGL, int THREADS, int EPT, bool VF, bool SIMPLE, bool CONV>
+__global__ void __launch_bounds__(THREADS, fft2_min_blocks<T, THREADS, EPT, CONV>())
+    fft2_kernel(const __grid_constant__ FftArgs<T> a) {
   typedef typename Cx<T>::t C;
   constexpr int E = THREADS * EPT, LOGE = ilog2c(E), LOGV = LOGE - LOGL, V = 1 << LOGV;
-  constexpr int L = 1 << LOGL;
   using S = Sched<LOGL>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
-  VecInfo* vinfo = reinterpret_cast<VecInfo*>(smem_raw + fft_vinfo_offset<C>(E));
+  VecInfo* vinfo = reinterpret_cast<VecInfo*>(smem_raw + fft2_vinfo_offset<C, LOGL>(E));
   const int64_t g0 = (int64_t)blockIdx.x * V;
   const int64_t nvec = a.ncu * a.outer * a.inner;
 
@@ -202,72 +264,18 @@ __global__ void __launch_bounds__(THREADS, fft2_min_blocks<T, THREADS, EPT>()) f
   }
   __syncthreads();
 
-  // load: every element of this thread first (all loads in flight together), then the
-  // shared-memory stores, in the order that is contiguous in HBM
-  C r[EPT];
-  if (SIMPLE) {
-    const C* in = reinterpret_cast<const C*>(a.in);
-    const int64_t ts = a.in_tstride;
-#pragma unroll
-    for (int i = 0; i < EPT; ++i) {
-      const int e = threadIdx.x + i * THREADS;
-      int t, v;
-      if (a.in_vcontig) { v = e & (V - 1); t = e >> LOGV; }
-      else { t = e & (L - 1); v = e >> LOGL; }
-      const int64_t off = vinfo[v].in_off;
-      r[i] = (off >= 0 && t < a.Lin) ? gld(in + off + t * ts) : cmake((T)0, (T)0);
-    }
-#pragma unroll
-    for (int i = 0; i < EPT; ++i) {
-      const int e = threadIdx.x + i * THREADS;
-      int t, v;
-      if (a.in_vcontig) { v = e & (V - 1); t = e >> LOGV; }
-      else { t = e & (L - 1); v = e >> LOGL; }
-      s[sp2<LOGL, LOGV>(t, v)] = r[i];
-    }
-  } else if (a.in_vcontig) {
-    // vectors fastest: with V <= THREADS each thread keeps one vector and t steps by
-    // THREADS / V, so the two-pass twiddle W^(t n2) follows a recurrence
-#pragma unroll
-    for (int i = 0; i < EPT; ++i) {
-      const int e = threadIdx.x + i * THREADS;
-      const int v = e & (V - 1), t = e >> LOGV;
-      r[i] = fft_load<T>(a, vinfo[v], t);
-    }
-    TwRec<T> tw(a.pre_tw, a.tw_mask, a.pre_tw_conj, vinfo, V <= THREADS, THREADS >> LOGV, LOGV);
-#pragma unroll
-    for (int i = 0; i < EPT; ++i) {
-      const int e = threadIdx.x + i * THREADS;
-      const int v = e & (V - 1), t = e >> LOGV;
-      s[sp2<LOGL, LOGV>(t, v)] = tw.apply(r[i], t, vinfo[v]);
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < EPT; ++i) {
-      const int e = threadIdx.x + i * THREADS;
-      const int t = e & (L - 1), v = e >> LOGL;
-      r[i] = fft_load<T>(a, vinfo[v], t);
-    }
-#pragma unroll
-    for (int i = 0; i < EPT; ++i) {
-      const int e = threadIdx.x + i * THREADS;
-      const int t = e & (L - 1), v = e >> LOGL;
-      s[sp2<LOGL, LOGV>(t, v)] = tw_direct<T>(r[i], a.pre_tw, a.tw_mask, a.pre_tw_conj, t, vinfo[v]);
-    }
-  }
-  __syncthreads();
-
   constexpr int LR0 = S::lr(0);
   constexpr int LRL = S::lr(S::NR - 1);
-  p2_read<C, THREADS, EPT, LOGL, LOGV, LR0>(r, s);
-  p2_run<C, THREADS, EPT, LOGL, LOGV, 0, false>(r, s, a.dir0, a.tw);
-  if (a.conv) {
+  C r[EPT];
+  load_first<T, VF, SIMPLE, THREADS, EPT, LOGL, LOGV, LR0>(r, a, vinfo);
+  p2_run<C, VF, THREADS, EPT, LOGL, LOGV, 0, false>(r, s, a.dir0, a.tw);
+  if constexpr (CONV) {
     // spectrum product at the natural positions t = j + k L/R of the last forward radix
     constexpr int R = 1 << LRL;
 #pragma unroll
     for (int q = 0; q < EPT / R; ++q) {
       int j, v;
-      bfly2<THREADS, LOGL, LOGV, LRL>(q, j, v);
+      bfly2<VF, THREADS, LOGL, LOGV, LRL>(q, j, v);
       const C* sp = a.spec + vinfo[v].soff + j;
 #pragma unroll
       for (int k = 0; k < R; ++k) {
@@ -275,61 +283,10 @@ __global__ void __launch_bounds__(THREADS, fft2_min_blocks<T, THREADS, EPT>()) f
         r[q * R + k] = cmul(r[q * R + k], a.spec_conj ? cconj(w) : w);
       }
     }
-    p2_run<C, THREADS, EPT, LOGL, LOGV, 0, true>(r, s, -a.dir0, a.tw);
-  }
-
-  // store, staged through shared memory
-  __syncthreads();
-  if (a.conv) p2_write<C, THREADS, EPT, LOGL, LOGV, LR0, LOGL - LR0>(r, s);
-  else p2_write<C, THREADS, EPT, LOGL, LOGV, LRL, LOGL - LRL>(r, s);
-  __syncthreads();
-  if (SIMPLE) {
-    C* out = reinterpret_cast<C*>(a.out);
-    const int64_t ts = a.out_tstride;
-#pragma unroll
-    for (int i = 0; i < EPT; ++i) {
-      const int e = threadIdx.x + i * THREADS;
-      int t, v;
-      if (a.out_vcontig) { v = e & (V - 1); t = e >> LOGV; }
-      else { t = e & (L - 1); v = e >> LOGL; }
-      r[i] = s[sp2<LOGL, LOGV>(t, v)];
-    }
-#pragma unroll
-    for (int i = 0; i < EPT; ++i) {
-      const int e = threadIdx.x + i * THREADS;
-      int t, v;
-      if (a.out_vcontig) { v = e & (V - 1); t = e >> LOGV; }
-      else { t = e & (L - 1); v = e >> LOGL; }
-      const int64_t off = vinfo[v].out_off;
-      if (off >= 0 && t < a.Lout) gst(out + off + t * ts, r[i]);
-    }
+    p2_run<C, VF, THREADS, EPT, LOGL, LOGV, 0, true>(r, s, -a.dir0, a.tw);
+    store_last<T, VF, SIMPLE, THREADS, EPT, LOGL, LOGV, LR0>(r, a, vinfo);
   } else {
-    // two phases in groups of 8 elements: the loads of the fused post operations (diagonal,
-    // row map) of a group first, then its stores
-    constexpr int G = EPT < 8 ? EPT : 8;
-    TwRec<T> tw(a.post_tw, a.tw_mask, a.post_tw_conj, vinfo, a.out_vcontig && V <= THREADS, THREADS >> LOGV, LOGV);
-#pragma unroll
-    for (int g = 0; g < EPT; g += G) {
-      int dst[G];
-#pragma unroll
-      for (int k = 0; k < G; ++k) {
-        const int e = threadIdx.x + (g + k) * THREADS;
-        int t, v;
-        if (a.out_vcontig) { v = e & (V - 1); t = e >> LOGV; }
-        else { t = e & (L - 1); v = e >> LOGL; }
-        C x = s[sp2<LOGL, LOGV>(t, v)];
-        x = a.out_vcontig ? tw.apply(x, t, vinfo[v])
-                          : tw_direct<T>(x, a.post_tw, a.tw_mask, a.post_tw_conj, t, vinfo[v]);
-        dst[k] = fft_store_prep<T>(a, vinfo[v], t, x);
-        r[g + k] = x;
-      }
-#pragma unroll
-      for (int k = 0; k < G; ++k) {
-        const int e = threadIdx.x + (g + k) * THREADS;
-        const int v = a.out_vcontig ? (e & (V - 1)) : (e >> LOGL);
-        fft_store_commit<T>(a, vinfo[v], dst[k], r[g + k]);
-      }
-    }
+    store_last<T, VF, SIMPLE, THREADS, EPT, LOGL, LOGV, LRL>(r, a, vinfo);
   }
 }
 
@@ -339,6 +296,31 @@ template <int LOGL, bool WIDE> struct TileCfg {
   static constexpr int THREADS = LOGE <= 12 ? 256 : 512;
   static constexpr int EPT = (1 << LOGE) / THREADS;
 };
+
+template <typename T, int LOGL, int THREADS, int EPT, bool VF, bool SIMPLE, bool CONV>
+fm_status fft2_start(const FftArgs<T>& a, int64_t tiles, size_t smem, cudaStream_t st) {
+  auto kern = fft2_kernel<T, LOGL, THREADS, EPT, VF, SIMPLE, CONV>;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  static std::atomic<unsigned long long> attr_bytes[32];
+  if (dev < 32 && attr_bytes[dev].load() < smem) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) { set_error("fft smem attribute: %s", cudaGetErrorString(e)); return FM_ERR_CUDA; }
+    attr_bytes[dev].store(smem);
+  }
+  kern<<<(unsigned)tiles, THREADS, smem, st>>>(a);
+  return after_launch("fft2_kernel");
+}
+
+template <typename T, int LOGL, int THREADS, int EPT, bool VF>
+fm_status fft2_pick(const FftArgs<T>& a, bool simple, int64_t tiles, size_t smem, cudaStream_t st) {
+  if (a.conv) {
+    return simple ? fft2_start<T, LOGL, THREADS, EPT, VF, true, true>(a, tiles, smem, st)
+                  : fft2_start<T, LOGL, THREADS, EPT, VF, false, true>(a, tiles, smem, st);
+  }
+  return simple ? fft2_start<T, LOGL, THREADS, EPT, VF, true, false>(a, tiles, smem, st)
+                : fft2_start<T, LOGL, THREADS, EPT, VF, false, false>(a, tiles, smem, st);
+}
 
 template <typename T, int LOGL, bool WIDE>
 fm_status fft2_launch_cfg(FftArgs<T> a, cudaStream_t st) {
@@ -357,21 +339,14 @@ fm_status fft2_launch_cfg(FftArgs<T> a, cudaStream_t st) {
   if (tiles > 0x7fffffffLL) { set_error("fft: too many tiles"); return FM_ERR_UNSUPPORTED; }
   a.in_vcontig = (a.inner > 1 || a.in_ostride == 1) ? 1 : 0;
   a.out_vcontig = (a.inner > 1 || a.out_ostride == 1) ? 1 : 0;
-  const size_t smem = fft_vinfo_offset<C>(E) + (size_t)V * sizeof(VecInfo);
+  const size_t smem = fft2_vinfo_offset<C, LOGL>(E) + (size_t)V * sizeof(VecInfo);
   const bool simple = a.in_mode == IO_C && a.out_mode == IO_C && !a.pre_map && !a.pre_dc && !a.pre_dr &&
                       !a.pre_tw && !a.post_tw && !a.post_dc && !a.post_dr && !a.post_map && a.scale == (T)1 &&
                       !a.beta && a.in_fmul == 1 && a.in_fmod == 1 && a.out_fmul == 1 && a.out_fmod == 1;
-  auto kern = simple ? fft2_kernel<T, LOGL, THREADS, EPT, true> : fft2_kernel<T, LOGL, THREADS, EPT, false>;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  static std::atomic<unsigned long long> attr_bytes[2][32];
-  if (dev < 32 && attr_bytes[simple][dev].load() < smem) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) { set_error("fft smem attribute: %s", cudaGetErrorString(e)); return FM_ERR_CUDA; }
-    attr_bytes[simple][dev].store(smem);
+  if constexpr (V > 1) {
+    if (a.in_vcontig) return fft2_pick<T, LOGL, THREADS, EPT, true>(a, simple, tiles, smem, st);
   }
-  kern<<<(unsigned)tiles, THREADS, smem, st>>>(a);
-  return after_launch("fft2_kernel");
+  return fft2_pick<T, LOGL, THREADS, EPT, false>(a, simple, tiles, smem, st);
 }
 
 template <typename T, int LOGL>

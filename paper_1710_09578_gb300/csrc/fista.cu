@@ -84,6 +84,7 @@ struct VState {
 template <int LOGL>
 struct FGeo {
   static constexpr int LOGV = 14 - LOGL, V = 1 << LOGV, NC = 1 << LOGL;
+  static constexpr bool VF = V >= 16;  // vectors fastest in shared memory
 };
 
 // x and y are rewritten by the kernel itself: read and write them through L2 (.cg), never
@@ -93,7 +94,7 @@ __device__ __forceinline__ void st_state(float* p, float2 v) { __stcg(reinterpre
 
 template <int LOGL>
 __device__ __forceinline__ float2* zaddr(float2* s, int t, int v) {
-  return &s[sp2<LOGL, FGeo<LOGL>::LOGV>(t, v)];
+  return &s[sp2<FGeo<LOGL>::VF, LOGL, FGeo<LOGL>::LOGV>(t, v)];
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -122,13 +123,14 @@ __device__ __forceinline__ void vec_max(VState* vs, int v, float val) {
 template <int LOGL>
 __device__ __forceinline__ void tile_fft(float2* s, int dir, const float2* tw) {
   constexpr int LOGV = FGeo<LOGL>::LOGV;
+  constexpr bool VF = FGeo<LOGL>::VF;
   using S = Sched<LOGL>;
   constexpr int LR0 = S::lr(0), LRL = S::lr(S::NR - 1);
   float2 r[kFEpt];
-  p2_read<float2, kFThreads, kFEpt, LOGL, LOGV, LR0>(r, s);
-  p2_run<float2, kFThreads, kFEpt, LOGL, LOGV, 0, false>(r, s, dir, tw);
+  p2_read<float2, VF, kFThreads, kFEpt, LOGL, LOGV, LR0>(r, s);
+  p2_run<float2, VF, kFThreads, kFEpt, LOGL, LOGV, 0, false>(r, s, dir, tw);
   __syncthreads();
-  p2_write<float2, kFThreads, kFEpt, LOGL, LOGV, LRL, LOGL - LRL>(r, s);
+  p2_write<float2, VF, kFThreads, kFEpt, LOGL, LOGV, LRL, LOGL - LRL>(r, s);
   __syncthreads();
 }
 
@@ -173,7 +175,7 @@ __device__ void tile_spectral(float2* s, VState* vs, int adjoint, const float2* 
 
 template <int LOGL>
 __device__ __forceinline__ float unpack(const float2* s, int m, int v) {
-  const float2 z = s[sp2<LOGL, FGeo<LOGL>::LOGV>(m >> 1, v)];
+  const float2 z = s[sp2<FGeo<LOGL>::VF, LOGL, FGeo<LOGL>::LOGV>(m >> 1, v)];
   return (m & 1) ? z.y : z.x;
 }
 

@@ -170,6 +170,26 @@ def test_hadamard_bf16_tensor_cores(fm, log2n, mode, tol):
     assert colerr(got_b, want) <= tol
 
 
+@pytest.mark.parametrize("log2n", [15, 16])
+def test_hadamard_long_columns_ld_and_sum(fm, log2n):
+    # long columns (two or four 2^14 blocks): padded leading dimensions on both sides, and
+    # a Sum whose second term accumulates into the first term's output
+    n = 1 << log2n
+    X = blk(3, n + 64, np.float32)
+    want = O.Hadamard(n).apply(X[:, :n].T.astype(np.float64)).T
+    Yg = torch.zeros((3, n + 32), dtype=torch.float32, device=DEV)
+    fm.hadamard(log2n).forward(gpu(X)[:, :n], out=Yg[:, :n])
+    assert colerr(Yg[:, :n].cpu().numpy(), want) <= tol32(n)
+    assert torch.count_nonzero(Yg[:, n:]).item() == 0
+    d = RNG.standard_normal(n).astype(np.float32)
+    S = fm.sum_(fm.hadamard(log2n), fm.hadamard(log2n), fm.diag(d))
+    got = S.forward(gpu(X)[:, :n]).cpu().numpy()
+    assert colerr(got, 2 * want + d * X[:, :n]) <= tol32(n)
+    Xi = RNG.integers(-128, 128, size=(3, n + 64)).astype(np.int8)
+    gi = fm.hadamard(log2n, fm.FM_HAD_INT8).forward(gpu(Xi)[:, :n]).cpu().numpy()
+    assert np.array_equal(gi.astype(np.int64), O.Hadamard(n).apply(Xi[:, :n].T.astype(np.int64)).T)
+
+
 def test_hadamard_bf16_workload_full(fm):
     xf, _ = I.hadamard_block()
     want = O.Hadamard(1 << 16).apply(xf.T.astype(np.float64)).T
