@@ -55,6 +55,34 @@ __device__ __forceinline__ void bfly2(int q, int& j, int& v) {
   }
 }
 
+// Elements t0 + k DT (k < R) of vector v: when the word step is a multiple of 16 the pad
+// slots between two of them are a constant too, so the addresses are one base plus
+// compile-time offsets.
+template <bool VF, int LOGL, int LOGV, int DT, int R, typename C>
+__device__ __forceinline__ void s_gather(C* x, const C* s, int t0, int v) {
+  constexpr int S = VF ? (DT << LOGV) : DT;
+  if constexpr (S % 16 == 0) {
+    const C* p = s + sp2<VF, LOGL, LOGV>(t0, v);
+#pragma unroll
+    for (int k = 0; k < R; ++k) x[k] = p[k * (S + S / 16)];
+  } else {
+#pragma unroll
+    for (int k = 0; k < R; ++k) x[k] = s[sp2<VF, LOGL, LOGV>(t0 + k * DT, v)];
+  }
+}
+template <bool VF, int LOGL, int LOGV, int DT, int R, typename C>
+__device__ __forceinline__ void s_scatter(const C* x, C* s, int t0, int v) {
+  constexpr int S = VF ? (DT << LOGV) : DT;
+  if constexpr (S % 16 == 0) {
+    C* p = s + sp2<VF, LOGL, LOGV>(t0, v);
+#pragma unroll
+    for (int k = 0; k < R; ++k) p[k * (S + S / 16)] = x[k];
+  } else {
+#pragma unroll
+    for (int k = 0; k < R; ++k) s[sp2<VF, LOGL, LOGV>(t0 + k * DT, v)] = x[k];
+  }
+}
+
 template <typename C, bool VF, int THREADS, int EPT, int LOGL, int LOGV, int LR>
 __device__ __forceinline__ void p2_read(C (&r)[EPT], const C* s) {
   constexpr int R = 1 << LR;
@@ -62,8 +90,7 @@ __device__ __forceinline__ void p2_read(C (&r)[EPT], const C* s) {
   for (int q = 0; q < EPT / R; ++q) {
     int j, v;
     bfly2<VF, THREADS, LOGL, LOGV, LR>(q, j, v);
-#pragma unroll
-    for (int k = 0; k < R; ++k) r[q * R + k] = s[sp2<VF, LOGL, LOGV>(j + (k << (LOGL - LR)), v)];
+    s_gather<VF, LOGL, LOGV, (1 << (LOGL - LR)), R>(&r[q * R], s, j, v);
   }
 }
 
@@ -76,8 +103,7 @@ __device__ __forceinline__ void p2_write(const C (&r)[EPT], C* s) {
     int j, v;
     bfly2<VF, THREADS, LOGL, LOGV, LR>(q, j, v);
     const int base = ((j >> LOGNS) << (LOGNS + LR)) + (j & ((1 << LOGNS) - 1));
-#pragma unroll
-    for (int k = 0; k < R; ++k) s[sp2<VF, LOGL, LOGV>(base + (k << LOGNS), v)] = r[q * R + k];
+    s_scatter<VF, LOGL, LOGV, (1 << LOGNS), R>(&r[q * R], s, base, v);
   }
 }
 
@@ -163,8 +189,7 @@ __device__ __forceinline__ void load_first(typename Cx<T>::t (&r)[EPT], const Ff
         r[q * R + k] = ok ? gld(unit ? in + k * M : in + k * step) : cmake((T)0, (T)0);
       }
     } else {
-#pragma unroll
-      for (int k = 0; k < R; ++k) r[q * R + k] = fft_load<T>(a, vi, j + k * M);
+      fft_load_bfly<T, R>(a, vi, j, M, &r[q * R]);
     }
   }
   if (!SIMPLE && a.pre_tw) {
@@ -199,11 +224,7 @@ __device__ __forceinline__ void store_last(typename Cx<T>::t (&r)[EPT], const Ff
       }
     } else {
       if (a.post_tw) tw_bfly<T, R>(&r[q * R], a.post_tw, a.tw_mask, a.post_tw_conj, j, M, vi.tw_n2);
-      int dst[R];
-#pragma unroll
-      for (int k = 0; k < R; ++k) dst[k] = fft_store_prep<T>(a, vi, j + k * M, r[q * R + k]);
-#pragma unroll
-      for (int k = 0; k < R; ++k) fft_store_commit<T>(a, vi, dst[k], r[q * R + k]);
+      fft_store_bfly<T, R>(a, vi, j, M, &r[q * R]);
     }
   }
 }
@@ -337,6 +358,13 @@ fm_status fft2_launch_cfg(FftArgs<T> a, cudaStream_t st) {
   if (nvec == 0) return FM_OK;
   const int64_t tiles = (nvec + V - 1) / V;
   if (tiles > 0x7fffffffLL) { set_error("fft: too many tiles"); return FM_ERR_UNSUPPORTED; }
+  // offsets inside a vector are 32-bit in the kernel
+  const int64_t lim = (int64_t)1 << 31;
+  if ((a.Lin + 1) * a.in_tstride >= lim || (a.Lout + 1) * a.out_tstride >= lim || a.L * a.in_fmul >= lim ||
+      a.L * a.out_fmul >= lim || a.Lin >= lim || a.Lout >= lim) {
+    set_error("fft: a vector spans 2^31 elements or more");
+    return FM_ERR_UNSUPPORTED;
+  }
   a.in_vcontig = (a.inner > 1 || a.in_ostride == 1) ? 1 : 0;
   a.out_vcontig = (a.inner > 1 || a.out_ostride == 1) ? 1 : 0;
   const size_t smem = fft2_vinfo_offset<C, LOGL>(E) + (size_t)V * sizeof(VecInfo);

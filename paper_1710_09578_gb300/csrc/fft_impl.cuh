@@ -39,72 +39,138 @@ __host__ __device__ constexpr size_t fft_vinfo_offset(int E) {
   return (((size_t)(E + E / 16 + 1) * sizeof(C)) + 15) & ~(size_t)15;
 }
 
-template <typename T>
-__device__ __forceinline__ typename Cx<T>::t fft_load(const FftArgs<T>& a, const VecInfo& vi, int t) {
+// The R inputs t = j + k M (k < R) of one butterfly of vector vi into x[0..R), with the
+// fused pre operations (row map P^H, diagonal, real-pair packing).  The uniform decisions
+// are taken once per butterfly, and offsets inside a vector are 32-bit: the launcher only
+// accepts vectors that span fewer than 2^31 elements.
+template <typename T, int R>
+__device__ __forceinline__ void fft_load_bfly(const FftArgs<T>& a, const VecInfo& vi, int j, int M,
+                                              typename Cx<T>::t* x) {
   typedef typename Cx<T>::t C;
-  if (vi.in_off < 0) return cmake((T)0, (T)0);
-  const int64_t n = (int64_t)t * a.in_fmul + vi.in_n2;
-  if (n >= a.Lin) return cmake((T)0, (T)0);
-  int64_t src = n;
-  if (a.pre_map) {
-    src = gld(a.pre_map + n);
-    if (src < 0) return cmake((T)0, (T)0);
+  const C zero = cmake((T)0, (T)0);
+  if (vi.in_off < 0) {
+#pragma unroll
+    for (int k = 0; k < R; ++k) x[k] = zero;
+    return;
   }
-  const int64_t off = vi.in_off + src * a.in_tstride;
-  C x;
-  if (a.in_mode == IO_C) {
-    x = gld(reinterpret_cast<const C*>(a.in) + off);
+  const int fmul = (int)a.in_fmul, Lin = (int)a.Lin, ts = (int)a.in_tstride;
+  const int n0 = j * fmul + vi.in_n2, dn = M * fmul;
+  int src[R];
+  if (a.pre_map) {
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int n = n0 + k * dn;
+      src[k] = n < Lin ? gld(a.pre_map + n) : -1;
+    }
   } else {
-    const T* p = reinterpret_cast<const T*>(a.in);
-    T re = gld(p + off);
-    T im = (a.in_mode == IO_RP && (vi.flags & 1)) ? gld(p + off + a.in_ld) : (T)0;
-    x = cmake(re, im);
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int n = n0 + k * dn;
+      src[k] = n < Lin ? n : -1;
+    }
+  }
+  if (a.in_mode == IO_C) {
+    const C* p = reinterpret_cast<const C*>(a.in) + vi.in_off;
+#pragma unroll
+    for (int k = 0; k < R; ++k) x[k] = src[k] >= 0 ? gld(p + src[k] * ts) : zero;
+  } else {
+    const T* p = reinterpret_cast<const T*>(a.in) + vi.in_off;
+    const bool two = a.in_mode == IO_RP && (vi.flags & 1);
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      T re = (T)0, im = (T)0;
+      if (src[k] >= 0) {
+        re = gld(p + src[k] * ts);
+        if (two) im = gld(p + src[k] * ts + a.in_ld);
+      }
+      x[k] = cmake(re, im);
+    }
   }
   if (a.pre_dc) {
-    C d = gld(a.pre_dc + n);
-    x = cmul(x, a.pre_conj ? cconj(d) : d);
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int n = n0 + k * dn;
+      if (n < Lin) {
+        const C d = gld(a.pre_dc + n);
+        x[k] = cmul(x[k], a.pre_conj ? cconj(d) : d);
+      }
+    }
   } else if (a.pre_dr) {
-    x = cscale(x, gld(a.pre_dr + n));
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int n = n0 + k * dn;
+      if (n < Lin) x[k] = cscale(x[k], gld(a.pre_dr + n));
+    }
   }
-  return x;
 }
 
-// Stores run in two phases so that the loads they need (diagonal, row map) are all issued
-// before the first store: prep applies the diagonal and the scale to x and returns the
-// destination row (-1: nothing to store); commit writes (or accumulates) x there.
-template <typename T>
-__device__ __forceinline__ int fft_store_prep(const FftArgs<T>& a, const VecInfo& vi, int t,
-                                              typename Cx<T>::t& x) {
+// The R outputs t = j + k M of one butterfly of vector vi, with the fused post operations
+// (diagonal, scale, row map P, accumulation, real-pair unpacking); every load the stores
+// need is issued before the first store.
+template <typename T, int R>
+__device__ __forceinline__ void fft_store_bfly(const FftArgs<T>& a, const VecInfo& vi, int j, int M,
+                                               typename Cx<T>::t* x) {
   typedef typename Cx<T>::t C;
-  if (vi.out_off < 0) return -1;
-  const int64_t n = (int64_t)t * a.out_fmul + vi.out_n2;
-  if (n >= a.Lout) return -1;
+  if (vi.out_off < 0) return;
+  const int fmul = (int)a.out_fmul, Lout = (int)a.Lout, ts = (int)a.out_tstride;
+  const int n0 = j * fmul + vi.out_n2, dn = M * fmul;
   if (a.post_dc) {
-    C d = gld(a.post_dc + n);
-    x = cmul(x, a.post_conj ? cconj(d) : d);
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int n = n0 + k * dn;
+      if (n < Lout) {
+        const C d = gld(a.post_dc + n);
+        x[k] = cmul(x[k], a.post_conj ? cconj(d) : d);
+      }
+    }
   } else if (a.post_dr) {
-    x = cscale(x, gld(a.post_dr + n));
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int n = n0 + k * dn;
+      if (n < Lout) x[k] = cscale(x[k], gld(a.post_dr + n));
+    }
   }
-  x = cscale(x, a.scale);
-  return a.post_map ? gld(a.post_map + n) : (int)n;
-}
-
-template <typename T>
-__device__ __forceinline__ void fft_store_commit(const FftArgs<T>& a, const VecInfo& vi, int dst,
-                                                 typename Cx<T>::t x) {
-  typedef typename Cx<T>::t C;
-  if (dst < 0) return;
-  const int64_t off = vi.out_off + (int64_t)dst * a.out_tstride;
-  if (a.out_mode == IO_C) {
-    C* p = reinterpret_cast<C*>(a.out) + off;
-    if (a.beta) x = cadd(x, gld(p));
-    gst(p, x);
+  if (a.scale != (T)1) {
+#pragma unroll
+    for (int k = 0; k < R; ++k) x[k] = cscale(x[k], a.scale);
+  }
+  int dst[R];
+  if (a.post_map) {
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int n = n0 + k * dn;
+      dst[k] = n < Lout ? gld(a.post_map + n) : -1;
+    }
   } else {
-    T* p = reinterpret_cast<T*>(a.out) + off;
-    gst(p, a.beta ? x.x + gld(p) : x.x);
-    if (a.out_mode == IO_RP && (vi.flags & 1)) {
-      p += a.out_ld;
-      gst(p, a.beta ? x.y + gld(p) : x.y);
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int n = n0 + k * dn;
+      dst[k] = n < Lout ? n : -1;
+    }
+  }
+  if (a.out_mode == IO_C) {
+    C* p = reinterpret_cast<C*>(a.out) + vi.out_off;
+    if (a.beta) {
+      C old[R];
+#pragma unroll
+      for (int k = 0; k < R; ++k) old[k] = dst[k] >= 0 ? gld(p + dst[k] * ts) : cmake((T)0, (T)0);
+#pragma unroll
+      for (int k = 0; k < R; ++k)
+        if (dst[k] >= 0) gst(p + dst[k] * ts, cadd(x[k], old[k]));
+    } else {
+#pragma unroll
+      for (int k = 0; k < R; ++k)
+        if (dst[k] >= 0) gst(p + dst[k] * ts, x[k]);
+    }
+  } else {
+    T* p = reinterpret_cast<T*>(a.out) + vi.out_off;
+    const bool two = a.out_mode == IO_RP && (vi.flags & 1);
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      if (dst[k] < 0) continue;
+      T* q = p + dst[k] * ts;
+      gst(q, a.beta ? x[k].x + gld(q) : x[k].x);
+      if (two) gst(q + a.out_ld, a.beta ? x[k].y + gld(q + a.out_ld) : x[k].y);
     }
   }
 }
