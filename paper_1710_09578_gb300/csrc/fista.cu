@@ -84,7 +84,10 @@ struct VState {
 template <int LOGL>
 struct FGeo {
   static constexpr int LOGV = 14 - LOGL, V = 1 << LOGV, NC = 1 << LOGL;
-  static constexpr bool VF = V >= 16;  // vectors fastest in shared memory
+  // elements of a vector contiguous in shared memory: the element-wise steps (spectral
+  // step, row mask, update) walk consecutive elements of one vector, and every transform
+  // length here (n >= 256) gives a warp 32 consecutive butterflies of one vector
+  static constexpr bool VF = false;
 };
 
 // x and y are rewritten by the kernel itself: read and write them through L2 (.cg), never

@@ -179,9 +179,10 @@ __global__ void __launch_bounds__(THREADS) fwht_tile_kernel(const __grid_constan
 // exchanges in between.  The first round loads straight from HBM with one 32-byte vector
 // load per block and register group (all C blocks combined with row r of H_C as they
 // arrive); the last round stores straight to HBM (128 contiguous bytes per warp and
-// instruction).  Shared-memory word of element e: e ^ (((e >> 8) & 3) << 3), which keeps
-// 32-byte groups intact and makes the round-B and round-C accesses bank-conflict free.
-__device__ __forceinline__ int lswz(int e) { return e ^ (((e >> 8) & 3) << 3); }
+// instruction).  Shared-memory word of element e: bits 3-4 XOR bits 8-9 and bit 2 XOR bit 5,
+// which keeps 16-byte groups intact and makes the round-A 16-byte stores and the round-B
+// and round-C accesses bank-conflict free.
+__device__ __forceinline__ int lswz(int e) { return e ^ (((e >> 8) & 3) << 3) ^ (((e >> 5) & 1) << 2); }
 
 template <typename W> struct Vec4;
 template <> struct Vec4<float> { typedef float4 t; };
@@ -232,9 +233,9 @@ __global__ void __launch_bounds__(512, 2) fwht_long_kernel(const Tin* __restrict
   wht_regs<W, 32>(r);
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    W* p = &s[lswz(8 * t + 4096 * q)];
-    *reinterpret_cast<V4*>(p) = make_vec4(r[8 * q], r[8 * q + 1], r[8 * q + 2], r[8 * q + 3]);
-    *reinterpret_cast<V4*>(p + 4) = make_vec4(r[8 * q + 4], r[8 * q + 5], r[8 * q + 6], r[8 * q + 7]);
+    *reinterpret_cast<V4*>(&s[lswz(8 * t + 4096 * q)]) = make_vec4(r[8 * q], r[8 * q + 1], r[8 * q + 2], r[8 * q + 3]);
+    *reinterpret_cast<V4*>(&s[lswz(8 * t + 4 + 4096 * q)]) =
+        make_vec4(r[8 * q + 4], r[8 * q + 5], r[8 * q + 6], r[8 * q + 7]);
   }
   __syncthreads();
 
@@ -329,6 +330,7 @@ fm_status fwht_launch(FwhtArgs a, fm_dtype in_dt, cudaStream_t st) {
   if (a.logL < 1) { set_error("fwht: n must be >= 2"); return FM_ERR_UNSUPPORTED; }
   if (in_dt == FM_F32 && long_path_ok(a, 4)) return fwht_long<float, float>(a, st);
   if (in_dt == FM_I8 && long_path_ok(a, 1)) return fwht_long<int8_t, int>(a, st);
+  if (fwht2_ok(a)) return fwht2_launch(a, in_dt, st);
   switch (in_dt) {
     case FM_F32: return fwht_cfg<float, float, float, 512, 32>(a, st);
     case FM_C64: return fwht_cfg<float2, float2, float2, 512, 16>(a, st);

@@ -22,6 +22,9 @@ struct FwhtArgs {
 };
 
 fm_status fwht_launch(FwhtArgs a, fm_dtype in_dt, cudaStream_t st);
+// Strided axes (inner >= 16), n <= 256: compile-time-length kernel (fwht2.cu).
+bool fwht2_ok(const FwhtArgs& a);
+fm_status fwht2_launch(const FwhtArgs& a, fm_dtype in_dt, cudaStream_t st);
 // BF16 tensor-core variants: split = 0 plain BF16 operands, 1 hi + lo split.
 fm_status fwht_mma_launch(FwhtArgs a, int split, cudaStream_t st);
 

@@ -294,6 +294,22 @@ def test_kron_three_factors(fm, shape):
     both(fm, A, ref, blk(3, n, np.complex64), blk(3, n, np.complex64), tol32(n))
 
 
+@pytest.mark.parametrize("dt", [np.float32, np.complex64])
+@pytest.mark.parametrize("la,lb", [(1, 6), (3, 5), (5, 4), (8, 4)])
+def test_kron_hadamard_strided_axis(fm, dt, la, lb):
+    # Hadamard along the outer axis of Kron(H, H, Diag): a strided axis with 16 or more
+    # vectors side by side (every transform length of the strided kernel), plus a Sum
+    # whose second term accumulates
+    d = RNG.standard_normal(4).astype(np.float32)
+    A = fm.kron(fm.hadamard(la), fm.hadamard(lb), fm.diag(d))
+    ref = O.Kron(O.Hadamard(1 << la), O.Hadamard(1 << lb), O.Diag(d))
+    n = ref.cols
+    both(fm, A, ref, blk(3, n, dt), blk(3, n, dt), tol32(n))
+    X = blk(2, n, dt)
+    got = fm.sum_(A, A).forward(gpu(X)).cpu().numpy()
+    assert colerr(got, 2 * ref.apply(X.T.astype(np.complex128)).T) <= tol32(n)
+
+
 def test_kron_mixed_and_nested(fm):
     idx = np.array([0, 2, 5], dtype=np.int32)
     d = I.cn(RNG, (8,))
