@@ -1,6 +1,6 @@
 // Tile FFT kernel with the transform length fixed at compile time.
 //
-// V vectors of length L per CTA, radix-8/4/2 Stockham passes with the elements of each
+// V vectors of length L per CTA, radix-16 (then 8/4/2) Stockham passes with the elements of each
 // butterfly in registers (the DFT of Eq. (1) by the butterfly factorisation of Sec. 1) and
 // the spectrum product of a circulant (Eq. (5)) in registers between the last forward and
 // the first inverse pass.  With L a template parameter the radix schedule, the
@@ -23,10 +23,32 @@ namespace fm {
 
 __host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x >> 1); }
 
+// Radix schedule (log2 of the radix of each pass, first to last): radix-16 passes where
+// they save an exchange through shared memory, radix 8 where a radix-2 pass would be left
+// over (measured on GB300: lengths 2^9 and 2^6 run faster as 8 x 8 x 8 and 8 x 8).
+__host__ __device__ constexpr int sched_lr(int logl, int p) {
+  constexpr int t[15][4] = {{0, 0, 0, 0}, {1, 0, 0, 0}, {2, 0, 0, 0}, {3, 0, 0, 0}, {4, 0, 0, 0},
+                            {3, 2, 0, 0}, {3, 3, 0, 0}, {4, 3, 0, 0}, {4, 4, 0, 0}, {3, 3, 3, 0},
+                            {4, 4, 2, 0}, {4, 4, 3, 0}, {4, 4, 4, 0}, {4, 4, 3, 2}, {4, 4, 4, 2}};
+  return t[logl][p];
+}
+__host__ __device__ constexpr int sched_nr(int logl) {
+  int n = 0;
+  while (n < 4 && sched_lr(logl, n) > 0) ++n;
+  return n;
+}
+
 template <int LOGL>
 struct Sched {
-  static constexpr int NR = (LOGL + 2) / 3;  // passes: radix 8, then one radix 4 or 2
-  __host__ __device__ static constexpr int lr(int p) { return p < LOGL / 3 ? 3 : LOGL - 3 * (LOGL / 3); }
+  static_assert(LOGL >= 1 && LOGL <= 14, "transform length 2^1 .. 2^14 per tile");
+  static constexpr int NR = sched_nr(LOGL);
+  __host__ __device__ static constexpr int lr(int p) { return sched_lr(LOGL, p); }
+  // log2 Ns before forward pass q (radices in order) and before inverse pass q (reversed)
+  __host__ __device__ static constexpr int ns_fwd(int q) {
+    int s = 0;
+    for (int i = 0; i < q; ++i) s += lr(i);
+    return s;
+  }
   __host__ __device__ static constexpr int ns_inv(int q) {
     int s = 0;
     for (int i = 0; i < q; ++i) s += lr(NR - 1 - i);
@@ -107,6 +129,33 @@ __device__ __forceinline__ void p2_write(const C (&r)[EPT], C* s) {
   }
 }
 
+// x[k] *= w^k for k = 1 .. R-1; the powers as a tree (w^2, w^4, w^8 by squaring, the rest
+// as one product of those), so the dependency chain stays short.
+template <typename C, int R>
+__device__ __forceinline__ void twiddle_powers(C* x, C w) {
+  if constexpr (R == 2) {
+    x[1] = cmul(x[1], w);
+  } else {
+    C p[R];
+    p[1] = w;
+    p[2] = cmul(w, w);
+    p[3] = cmul(p[2], w);
+    if constexpr (R >= 8) {
+      p[4] = cmul(p[2], p[2]);
+      p[5] = cmul(p[4], w);
+      p[6] = cmul(p[4], p[2]);
+      p[7] = cmul(p[4], p[3]);
+    }
+    if constexpr (R == 16) {
+      p[8] = cmul(p[4], p[4]);
+#pragma unroll
+      for (int k = 9; k < 16; ++k) p[k] = cmul(p[8], p[k - 8]);
+    }
+#pragma unroll
+    for (int k = 1; k < R; ++k) x[k] = cmul(x[k], p[k]);
+  }
+}
+
 template <typename C, bool VF, int THREADS, int EPT, int LOGL, int LOGV, int LR, int LOGNS>
 __device__ __forceinline__ void p2_compute(C (&r)[EPT], int dir, const C* __restrict__ tw) {
   constexpr int R = 1 << LR;
@@ -117,14 +166,10 @@ __device__ __forceinline__ void p2_compute(C (&r)[EPT], int dir, const C* __rest
       bfly2<VF, THREADS, LOGL, LOGV, LR>(q, j, v);
       C w = gld(tw + ((j & ((1 << LOGNS) - 1)) << (kTwLog - LOGNS - LR)));
       if (dir > 0) w = cconj(w);
-      C wk = w;
-#pragma unroll
-      for (int k = 1; k < R; ++k) {
-        r[q * R + k] = cmul(r[q * R + k], wk);
-        if (k + 1 < R) wk = cmul(wk, w);
-      }
+      twiddle_powers<C, R>(&r[q * R], w);
     }
-    if (R == 8) dft8(&r[q * R], dir);
+    if (R == 16) dft16(&r[q * R], dir);
+    else if (R == 8) dft8(&r[q * R], dir);
     else if (R == 4) dft4(&r[q * R], dir);
     else dft2(&r[q * R]);
   }
@@ -135,7 +180,7 @@ __device__ __forceinline__ void p2_run(C (&r)[EPT], C* s, int dir, const C* tw) 
   using S = Sched<LOGL>;
   if constexpr (P < S::NR) {
     constexpr int LR = INV ? S::lr(S::NR - 1 - P) : S::lr(P);
-    constexpr int LOGNS = INV ? S::ns_inv(P) : 3 * P;
+    constexpr int LOGNS = INV ? S::ns_inv(P) : S::ns_fwd(P);
     if constexpr (P > 0) p2_read<C, VF, THREADS, EPT, LOGL, LOGV, LR>(r, s);
     p2_compute<C, VF, THREADS, EPT, LOGL, LOGV, LR, LOGNS>(r, dir, tw);
     if constexpr (P + 1 < S::NR) {
@@ -189,15 +234,21 @@ __device__ __forceinline__ void load_first(typename Cx<T>::t (&r)[EPT], const Ff
         r[q * R + k] = ok ? gld(unit ? in + k * M : in + k * step) : cmake((T)0, (T)0);
       }
     } else {
-      fft_load_bfly<T, R>(a, vi, j, M, &r[q * R]);
+      // fused loads in runs of at most 8 (registers: each run keeps its row indices live)
+      constexpr int H = R > 8 ? 8 : R;
+#pragma unroll
+      for (int h = 0; h < R; h += H) fft_load_bfly<T, H>(a, vi, j + h * M, M, &r[q * R + h]);
     }
   }
   if (!SIMPLE && a.pre_tw) {
+    constexpr int H = R > 8 ? 8 : R;
 #pragma unroll
     for (int q = 0; q < EPT / R; ++q) {
       int j, v;
       bfly2<VF, THREADS, LOGL, LOGV, LR>(q, j, v);
-      tw_bfly<T, R>(&r[q * R], a.pre_tw, a.tw_mask, a.pre_tw_conj, j, M, vinfo[v].tw_n2);
+#pragma unroll
+      for (int h = 0; h < R; h += H)
+        tw_bfly<T, H>(&r[q * R + h], a.pre_tw, a.tw_mask, a.pre_tw_conj, j + h * M, M, vinfo[v].tw_n2);
     }
   }
 }
@@ -223,8 +274,12 @@ __device__ __forceinline__ void store_last(typename Cx<T>::t (&r)[EPT], const Ff
         if (vi.out_off >= 0 && j + k * M < a.Lout) gst(unit ? out + k * M : out + k * step, r[q * R + k]);
       }
     } else {
-      if (a.post_tw) tw_bfly<T, R>(&r[q * R], a.post_tw, a.tw_mask, a.post_tw_conj, j, M, vi.tw_n2);
-      fft_store_bfly<T, R>(a, vi, j, M, &r[q * R]);
+      constexpr int H = R > 8 ? 8 : R;
+#pragma unroll
+      for (int h = 0; h < R; h += H) {
+        if (a.post_tw) tw_bfly<T, H>(&r[q * R + h], a.post_tw, a.tw_mask, a.post_tw_conj, j + h * M, M, vi.tw_n2);
+        fft_store_bfly<T, H>(a, vi, j + h * M, M, &r[q * R + h]);
+      }
     }
   }
 }

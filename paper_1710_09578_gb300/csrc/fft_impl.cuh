@@ -1,7 +1,7 @@
 // Batched Stockham FFT engine for the Fourier, Circulant and Toeplitz operators.
 //
 // One CTA owns a tile of V vectors of length L (L * V = THREADS * EPT elements) in
-// shared memory and runs radix-8/4/2 Stockham passes over it: each thread keeps EPT
+// shared memory and runs radix-16/8/4/2 Stockham passes over it: each thread keeps EPT
 // elements in registers, multiplies by the twiddles of the pass, does the small DFT in
 // registers and writes the results to their auto-sorted place, so no bit reversal is
 // ever needed (the DFT of Eq. (1), evaluated by the butterfly factorisation the paper

@@ -60,6 +60,60 @@ template <typename C> __device__ __forceinline__ void dft8(C* a, int dir) {
   a[7] = csub(e[3], o3);
 }
 
+// x * W_16^m with W_16 = exp(dir * 2 pi i / 16), for the nine exponents of a 4 x 4 split.
+template <typename C, int M>
+__device__ __forceinline__ C w16(C x, int dir) {
+  typedef decltype(x.x) T;
+  constexpr int m = M % 16;
+  if constexpr (m == 0) return x;
+  else if constexpr (m == 4) return cmul_i(x, dir);
+  else if constexpr (m == 8) return cmake(-x.x, -x.y);
+  else if constexpr (m == 12) return cmul_i(x, -dir);
+  else {
+    // cos and sin of 2 pi m / 16 for m = 1, 2, 3, 6, 9 (the only other exponents used)
+    const T c1 = (T)0.92387953251128675612818318939678828682, s1 = (T)0.38268343236508977172845998403039886676;
+    const T h = (T)0.70710678118654752440084436210484903928;
+    T c, sn;
+    if constexpr (m == 1) { c = c1; sn = s1; }
+    else if constexpr (m == 2) { c = h; sn = h; }
+    else if constexpr (m == 3) { c = s1; sn = c1; }
+    else if constexpr (m == 6) { c = -h; sn = h; }
+    else { c = -c1; sn = -s1; }  // m == 9
+    const T sd = dir > 0 ? sn : -sn;
+    return cmake(x.x * c - x.y * sd, x.x * sd + x.y * c);
+  }
+}
+
+// In-register DFT of size 16 (natural order in and out) as 4 x 4: DFTs of length 4 over
+// the stride-4 subsequences, twiddles W_16^(i k1), DFTs of length 4 across them; the
+// result index k1 + 4 k2 is a renaming of registers.
+template <typename C> __device__ __forceinline__ void dft16(C* a, int dir) {
+  C b[16];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    C t[4] = {a[i], a[i + 4], a[i + 8], a[i + 12]};
+    dft4(t, dir);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) b[4 * i + k1] = t[k1];
+  }
+  b[5] = w16<C, 1>(b[5], dir);
+  b[6] = w16<C, 2>(b[6], dir);
+  b[7] = w16<C, 3>(b[7], dir);
+  b[9] = w16<C, 2>(b[9], dir);
+  b[10] = w16<C, 4>(b[10], dir);
+  b[11] = w16<C, 6>(b[11], dir);
+  b[13] = w16<C, 3>(b[13], dir);
+  b[14] = w16<C, 6>(b[14], dir);
+  b[15] = w16<C, 9>(b[15], dir);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    C t[4] = {b[k1], b[4 + k1], b[8 + k1], b[12 + k1]};
+    dft4(t, dir);
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) a[k1 + 4 * k2] = t[k2];
+  }
+}
+
 // Global-space loads and stores.  With the state space explicit (rather than a generic
 // address that might point into shared memory) the instruction scheduler may move a load
 // ahead of unrelated shared-memory stores, so a thread can have all the loads of a tile in
