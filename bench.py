@@ -356,10 +356,13 @@ def measure_rows(fm, torch, dev, stream, flush, xi, cpu_sample=True):
     Ygo = torch.empty((64, m), dtype=torch.complex64, device=dev)
     Zg = torch.empty((64, n), dtype=torch.complex64, device=dev)
     A.reserve(64, torch.complex64)
+    # set-up: calibrate the two-pass split of the length-2^18 circulant for 64 columns
+    tune = A.calibrate(64, torch.complex64)
     byts = 2 * (64 * n * 8 + 64 * m * 8 + n * 8 * 2 + m * 4)
     rows["cs_PDC_2p18x64_fwd+adj"] = {
         "GB/s": _gbs_loop(lambda: (A.forward(Xg, out=Ygo), A.backward(Ygo, out=Zg)), byts, 50, flush, stream,
-                          torch), "algorithmic_bytes": byts}
+                          torch), "algorithmic_bytes": byts,
+        "calibrated_split": [[e["L"], e["n1"]] for e in tune]}
     del Xg, Ygo, Zg, A
     # Kron(H_256, C_1024, F_64), N = 2^24, 4 complex64 columns
     ck, Xk, _ = I.kron_large()

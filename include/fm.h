@@ -169,6 +169,36 @@ fm_status fm_reserve(fm_op A, int64_t ncols, fm_dtype xdt, void* stream);
 fm_status fm_circulant_apply_noalloc(fm_op C, int adjoint, const void* X, int64_t ldx, void* Y, int64_t ldy,
                                      int64_t ncols, void* stream);
 
+/* ---------------------------------------------------------------- calibration */
+
+/* Calibration of the execution plan: the GPU form of the paper's calibration step
+ * (Sec. 2.1.3), which times an operator's transforms and keeps what it learns.  A
+ * transform longer than one tile (Fourier, Circulant or Toeplitz embedding of length
+ * L > 8192) runs as two passes over an N1 x N2 split of L; which split is fastest depends
+ * on the operator (a convolution or a plain transform, the fused neighbours) and on the
+ * number of columns.  fm_calibrate times A's forward + adjoint on ncols probe columns of
+ * complex_of(dt) for each candidate split of each such transform in A (N1 = 2^e with both
+ * N1 and N2 between 2^5 and 2^13), one transform at a time, and keeps the fastest in A.
+ * Results are unchanged up to FP rounding.  It allocates and frees its probe buffers and
+ * synchronises `stream`; A must not be in use on another stream meanwhile.
+ * report (host, optional): one entry per tuned transform, at most max_entries; *n_entries
+ * (optional) receives the number of tuned transforms.  A without such a transform: FM_OK,
+ * *n_entries = 0. */
+typedef struct {
+  int64_t L;            /* transform length */
+  int64_t n1;           /* chosen N1 (N2 = L / N1) */
+  int32_t ncand;        /* candidates timed (<= 8) */
+  int64_t cand_n1[8];   /* their N1 */
+  float ms[8];          /* forward + adjoint of A with that split, milliseconds */
+} fm_tune_entry;
+fm_status fm_calibrate(fm_op A, int64_t ncols, fm_dtype dt, void* stream, fm_tune_entry* report,
+                       int32_t max_entries, int32_t* n_entries);
+/* Set N1 of every two-pass transform of length L in A (n1 = 0: the default 2^floor(log2(L)/2)),
+ * e.g. to restore a calibration result.  FM_ERR_INVALID_ARG if n1 is not a power of two with
+ * N1, L / N1 in [2^5, 2^13]; FM_OK if A has no transform of length L.  Same rules about
+ * concurrent use as fm_calibrate. */
+fm_status fm_set_split(fm_op A, int64_t L, int64_t n1, void* stream);
+
 /* ---------------------------------------------------------------- FISTA */
 
 /* Batched FISTA (accelerated proximal gradient, cited in Sec. 3) for

@@ -124,6 +124,39 @@ class Op:
         """Grow the workspace so that later calls on up to ncols columns allocate nothing."""
         _lib.fm_reserve(self._h, ncols, _TORCH2FM[dtype], _stream())
 
+    def calibrate(self, ncols: int, dtype: torch.dtype = torch.complex64, cache: str | None = None,
+                  key: str | None = None):
+        """Pick the fastest two-pass split for every long transform in this operator by timing
+        forward + adjoint on ncols probe columns (the GPU form of the paper's calibration).
+
+        With `cache` (a JSON file path) the result is stored under `key` (default: shape,
+        ncols and dtype) and a later call with the same key restores it without timing.
+        Returns the list of {"L", "n1", "ms"} entries that were applied."""
+        import json
+        import os
+        key = key or f"{self.shape[0]}x{self.shape[1]}:{ncols}:{str(dtype).replace('torch.', '')}"
+        table = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as f:
+                table = json.load(f)
+        if key in table:
+            for e in table[key]:
+                _lib.fm_set_split(self._h, int(e["L"]), int(e["n1"]), _stream())
+            return table[key]
+        res = _lib.fm_calibrate(self._h, ncols, _TORCH2FM[dtype], _stream())
+        if cache:
+            table[key] = [{"L": e["L"], "n1": e["n1"], "ms": {str(k): v for k, v in e["ms"].items()}}
+                          for e in res]
+            tmp = cache + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(table, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
+        return res
+
+    def set_split(self, L: int, n1: int):
+        """Use the split N1 x (L / N1) for every two-pass transform of length L (0: default)."""
+        _lib.fm_set_split(self._h, L, n1, _stream())
+
     def __matmul__(self, other):
         if isinstance(other, Op):
             return product(self, other)

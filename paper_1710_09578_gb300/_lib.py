@@ -37,6 +37,11 @@ class fm_fista_report(ctypes.Structure):
                 ("objective", ctypes.c_void_p), ("status", ctypes.c_void_p)]
 
 
+class fm_tune_entry(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int64), ("n1", ctypes.c_int64), ("ncand", ctypes.c_int32),
+                ("cand_n1", ctypes.c_int64 * 8), ("ms", ctypes.c_float * 8)]
+
+
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"CUDA library not built: {LIB_PATH} is missing (run __graft_entry__.build())")
 lib = ctypes.CDLL(LIB_PATH)
@@ -69,6 +74,8 @@ _SIGS = {
     "fm_batch_create": [_opp, _i64, _p, _opp],
     "fm_batch_sizes": [_p, ctypes.POINTER(_i64), ctypes.POINTER(_i64)],
     "fm_fista": [_p, _p, _p, ctypes.POINTER(fm_fista_params), ctypes.POINTER(fm_fista_report), _p],
+    "fm_calibrate": [_op, _i64, _i32, _p, ctypes.POINTER(fm_tune_entry), _i32, ctypes.POINTER(_i32)],
+    "fm_set_split": [_op, _i64, _i64, _p],
 }
 for _name, _args in _SIGS.items():
     getattr(lib, _name).argtypes = _args
@@ -178,6 +185,23 @@ def fm_backward(h, Y: int, ldy: int, ydt: int, X: int, ldx: int, xdt: int, ncols
 
 def fm_reserve(h, ncols: int, xdt: int, stream: int = 0):
     check(lib.fm_reserve(h, ncols, xdt, stream), "fm_reserve")
+
+
+def fm_calibrate(h, ncols: int, dt: int, stream: int = 0):
+    """Time the candidate splits of every two-pass transform of h; returns one dict per
+    tuned transform: L, chosen n1, and {n1: ms} for the candidates."""
+    rep = (fm_tune_entry * 64)()
+    n = _i32(0)
+    check(lib.fm_calibrate(h, ncols, dt, stream, rep, 64, ctypes.byref(n)), "fm_calibrate")
+    out = []
+    for e in rep[:min(n.value, 64)]:
+        out.append({"L": int(e.L), "n1": int(e.n1),
+                    "ms": {int(e.cand_n1[i]): float(e.ms[i]) for i in range(e.ncand)}})
+    return out
+
+
+def fm_set_split(h, L: int, n1: int, stream: int = 0):
+    check(lib.fm_set_split(h, L, n1, stream), "fm_set_split")
 
 
 def fm_circulant_apply_noalloc(h, adjoint: int, X: int, ldx: int, Y: int, ldy: int, ncols: int,

@@ -1,0 +1,178 @@
+// Calibration of the two-pass split of long transforms (fm_calibrate, fm_set_split).
+//
+// The paper's calibration (Sec. 2.1.3) benchmarks the fast transforms of an operator and
+// stores what it finds for later decisions.  Here the decision is the split L = N1 x N2
+// of a transform longer than one tile: the column pass (length N1, stride N2) and the row
+// pass (length N2, with the spectrum product for a convolution) cost differently, and the
+// cheapest split depends on the operator and the column count.  The candidates are timed
+// on the operator as a whole (forward + adjoint, CUDA events) and the best one is kept.
+#include <algorithm>
+#include <vector>
+
+#include "fm_internal.h"
+
+namespace fm {
+namespace {
+
+__global__ void spec_permute_kernel(const double2* s64, double2* p64, float2* p32, int64_t L, int64_t N1,
+                                    int64_t N2) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < L; k += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = s64[k];
+    const int64_t k1 = k % N1, k2 = k / N1;
+    p64[k1 * N2 + k2] = v;
+    p32[k1 * N2 + k2] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+int ilog2_64(int64_t x) {
+  int l = 0;
+  while ((1LL << l) < x) ++l;
+  return l;
+}
+
+void collect(fm_op_s* A, std::vector<fm_op_s*>& out) {
+  if (!A) return;
+  if ((A->kind == K_FOURIER || A->kind == K_CIRCULANT || A->kind == K_TOEPLITZ) && A->big.L) {
+    if (std::find(out.begin(), out.end(), A) == out.end()) out.push_back(A);
+  }
+  for (fm_op_s* k : A->kids) collect(k, out);
+}
+
+bool split_ok(int64_t L, int64_t n1) {
+  if (n1 < 32 || (n1 & (n1 - 1)) || L % n1) return false;
+  const int64_t n2 = L / n1;
+  return n1 <= 8192 && n2 >= 32 && n2 <= 8192;
+}
+
+fm_status set_leaf_split(fm_op_s* A, int64_t n1, cudaStream_t st) {
+  const int64_t L = A->big.L;
+  if (n1 == A->big.N1) return FM_OK;
+  A->big.N1 = n1;
+  A->big.N2 = L / n1;
+  if (A->spec64 && A->spec64_perm) {
+    int64_t blocks = (L + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    spec_permute_kernel<<<(unsigned)blocks, 256, 0, st>>>(A->spec64, A->spec64_perm, A->spec32_perm, L, n1, L / n1);
+    FM_TRY(after_launch("spec_permute_kernel"));
+  }
+  return FM_OK;
+}
+
+}  // namespace
+}  // namespace fm
+
+using namespace fm;
+
+extern "C" {
+
+fm_status fm_set_split(fm_op A, int64_t L, int64_t n1, void* stream) {
+  clear_error();
+  if (!A) { set_error("null operator"); return FM_ERR_INVALID_ARG; }
+  if (n1 == 0) n1 = (int64_t)1 << (ilog2_64(L) / 2);
+  if (!split_ok(L, n1)) {
+    set_error("split %lld x %lld of %lld: N1 and N2 must be powers of two in [2^5, 2^13]", (long long)n1,
+              (long long)(n1 ? L / n1 : 0), (long long)L);
+    return FM_ERR_INVALID_ARG;
+  }
+  std::vector<fm_op_s*> leaves;
+  collect(A, leaves);
+  cudaStream_t st = (cudaStream_t)stream;
+  for (fm_op_s* leaf : leaves)
+    if (leaf->big.L == L) FM_TRY(set_leaf_split(leaf, n1, st));
+  FM_CUDA(cudaStreamSynchronize(st));
+  return FM_OK;
+}
+
+fm_status fm_calibrate(fm_op A, int64_t ncols, fm_dtype dt, void* stream, fm_tune_entry* report,
+                       int32_t max_entries, int32_t* n_entries) {
+  clear_error();
+  if (n_entries) *n_entries = 0;
+  if (!A || ncols <= 0) { set_error("bad argument"); return FM_ERR_INVALID_ARG; }
+  if (dt != FM_F32 && dt != FM_F64 && dt != FM_C64 && dt != FM_C128) { set_error("calibration dtype"); return FM_ERR_DTYPE; }
+  std::vector<fm_op_s*> leaves;
+  collect(A, leaves);
+  if (leaves.empty()) return FM_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const fm_dtype cdt = complex_of(dt);
+  const size_t esz = (size_t)dtype_size(cdt);
+  void *X = nullptr, *Y = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  fm_status s = FM_OK;
+  auto cleanup = [&]() {
+    if (X) cudaFree(X);
+    if (Y) cudaFree(Y);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  if (cudaMalloc(&X, esz * (size_t)A->cols * ncols) != cudaSuccess ||
+      cudaMalloc(&Y, esz * (size_t)A->rows * ncols) != cudaSuccess) {
+    cleanup();
+    set_error("calibration: no memory for %lld probe columns", (long long)ncols);
+    return FM_ERR_OOM;
+  }
+  cudaMemsetAsync(X, 0, esz * (size_t)A->cols * ncols, st);
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto time_once = [&](float* ms) -> fm_status {
+    // one warm-up, then the mean of three forward + adjoint pairs
+    FM_TRY(fm_forward(A, X, A->cols, cdt, Y, A->rows, cdt, ncols, st));
+    FM_TRY(fm_backward(A, Y, A->rows, cdt, X, A->cols, cdt, ncols, st));
+    FM_CUDA(cudaEventRecord(e0, st));
+    for (int r = 0; r < 3; ++r) {
+      FM_TRY(fm_forward(A, X, A->cols, cdt, Y, A->rows, cdt, ncols, st));
+      FM_TRY(fm_backward(A, Y, A->rows, cdt, X, A->cols, cdt, ncols, st));
+    }
+    FM_CUDA(cudaEventRecord(e1, st));
+    FM_CUDA(cudaEventSynchronize(e1));
+    FM_CUDA(cudaEventElapsedTime(ms, e0, e1));
+    *ms /= 3.f;
+    return FM_OK;
+  };
+  int32_t done = 0;
+  for (fm_op_s* leaf : leaves) {
+    const int64_t L = leaf->big.L;
+    const int lg = ilog2_64(L);
+    std::vector<int64_t> cand;
+    for (int e : {lg / 2, 6, 5, 7, lg - 13, lg - 12}) {
+      const int64_t n1 = (int64_t)1 << std::max(e, 0);
+      if (split_ok(L, n1) && std::find(cand.begin(), cand.end(), n1) == cand.end()) cand.push_back(n1);
+    }
+    const int64_t start = leaf->big.N1;
+    int64_t best = start;
+    float best_ms = 0.f;
+    fm_tune_entry ent = {};
+    ent.L = L;
+    for (int64_t n1 : cand) {
+      if (ent.ncand >= 8) break;
+      s = set_leaf_split(leaf, n1, st);
+      float ms = 0.f;
+      if (s == FM_OK) s = time_once(&ms);
+      if (s != FM_OK) break;
+      ent.cand_n1[ent.ncand] = n1;
+      ent.ms[ent.ncand] = ms;
+      ent.ncand++;
+      if (best_ms == 0.f || ms < best_ms) {
+        best_ms = ms;
+        best = n1;
+      }
+    }
+    fm_status s2 = set_leaf_split(leaf, s == FM_OK ? best : start, st);
+    if (s == FM_OK) s = s2;
+    if (s != FM_OK) break;
+    ent.n1 = best;
+    if (report && done < max_entries) report[done] = ent;
+    ++done;
+  }
+  if (s == FM_OK) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      set_error("calibration: %s", cudaGetErrorString(e));
+      s = FM_ERR_CUDA;
+    }
+  }
+  cleanup();
+  if (n_entries) *n_entries = done;
+  return s;
+}
+
+}  // extern "C"

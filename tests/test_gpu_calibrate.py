@@ -1,0 +1,102 @@
+"""GPU: calibration of the two-pass split (fm_calibrate / fm_set_split).
+
+Every split the calibration may choose must give the oracle's result; the calibration must
+pick one of its candidates and keep the operator correct; the JSON cache must restore a
+stored choice without timing.
+"""
+import json
+
+import numpy as np
+import pytest
+
+import fm_inputs as I
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def fm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1710_09578_gb300 as fm
+    return fm
+
+
+RNG = np.random.default_rng(77)
+
+
+def colerr(got, want):
+    got = np.asarray(got, dtype=np.complex128).reshape(want.shape)
+    num = np.linalg.norm(got - want, axis=-1)
+    den = np.maximum(np.linalg.norm(want, axis=-1), 1e-300)
+    return float(np.max(num / den))
+
+
+def gpu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def _cs(n, seed):
+    rng = np.random.default_rng(seed)
+    c = np.where(rng.integers(0, 2, n) == 1, 1.0, -1.0)
+    d = np.exp(2j * np.pi * rng.random(n)).astype(np.complex64)
+    idx = np.sort(rng.choice(n, n // 4, replace=False)).astype(np.int32)
+    return c, d, idx
+
+
+def _check(A, ref, X, Y, tol):
+    ef = colerr(A.forward(gpu(X)).cpu().numpy(), ref.apply(X.T).T)
+    eb = colerr(A.backward(gpu(Y)).cpu().numpy(), ref.apply(Y.T, adjoint=True).T)
+    assert ef <= tol and eb <= tol, (ef, eb, tol)
+
+
+@pytest.mark.parametrize("n1", [32, 64, 128, 512, 2048, 8192])
+def test_every_split_matches_oracle(fm, n1):
+    n = 1 << 18
+    c, d, idx = _cs(n, 5)
+    A = fm.product(fm.partial(idx, n), fm.diag(d), fm.circulant(c))
+    ref = O.Product(O.Partial(idx, n), O.Diag(d), O.Circulant(c))
+    A.set_split(n, n1)
+    X = I.column_block(RNG, 2, n, np.complex64)
+    Y = I.column_block(RNG, 2, n // 4, np.complex64)
+    _check(A, ref, X, Y, 1e-5 * 18)
+    F = fm.fourier(n)
+    F.set_split(n, n1)
+    _check(F, O.Fourier(n), X, X, 1e-5 * 18)
+
+
+def test_calibrate_picks_a_candidate_and_stays_correct(fm, tmp_path):
+    n = 1 << 18
+    c, d, idx = _cs(n, 6)
+    A = fm.product(fm.partial(idx, n), fm.diag(d), fm.circulant(c))
+    ref = O.Product(O.Partial(idx, n), O.Diag(d), O.Circulant(c))
+    cache = str(tmp_path / "tune.json")
+    res = A.calibrate(8, torch.complex64, cache=cache)
+    assert len(res) == 1 and res[0]["L"] == n
+    assert res[0]["n1"] in res[0]["ms"] and len(res[0]["ms"]) >= 2
+    assert all(v > 0 for v in res[0]["ms"].values())
+    X = I.column_block(RNG, 2, n, np.complex64)
+    Y = I.column_block(RNG, 2, n // 4, np.complex64)
+    _check(A, ref, X, Y, 1e-5 * 18)
+    # a second operator restores the stored split from the cache without timing
+    with open(cache) as f:
+        stored = json.load(f)
+    assert len(stored) == 1
+    B = fm.product(fm.partial(idx, n), fm.diag(d), fm.circulant(c))
+    again = B.calibrate(8, torch.complex64, cache=cache)
+    assert again[0]["n1"] == res[0]["n1"]
+    _check(B, ref, X, Y, 1e-5 * 18)
+
+
+def test_split_rules(fm):
+    F = fm.fourier(1 << 16)
+    with pytest.raises(fm.FmError):
+        F.set_split(1 << 16, 48)          # not a power of two
+    with pytest.raises(fm.FmError):
+        F.set_split(1 << 16, 4)           # N2 = 2^14 above one FP64 tile
+    F.set_split(1 << 12, 64)              # no transform of that length: nothing to do
+    F.set_split(1 << 16, 0)               # back to the default
+    assert fm.fourier(1024).calibrate(4) == []   # single-tile transforms: nothing to tune
