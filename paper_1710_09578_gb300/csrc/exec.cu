@@ -11,6 +11,7 @@
 #include <cstring>
 
 #include "exec.h"
+#include "kron_hf.h"
 #include "fft.h"
 #include "fwht.h"
 #include "pointwise.h"
@@ -651,7 +652,50 @@ static fm_status exec_kron(const fm_op_s* A, bool adj, const View& in, const Vie
   const size_t mark = ctx.used;
   View src = in;
   src.ostride = in.n * in.inner;
-  for (int j = 0; j < k; ++j) {
+  // Hadamard outermost and Fourier innermost on complex64 columns: both in one fused pass
+  // (the mode products commute), then the middle factors as usual
+  const fm_op_s* f0 = A->kids[0];
+  const fm_op_s* fl = A->kids[k - 1];
+  int la = 0, lb = 0;
+  while ((1LL << lb) < fl->L) ++lb;
+  la = f0->log2n;
+  const bool fuse = f0->kind == K_HADAMARD && f0->had_mode == FM_HAD_FP32 && fl->kind == K_FOURIER &&
+                    in.dt == FM_C64 && out.dt == FM_C64 && in.outer == 1 && in.inner == 1 && out.outer == 1 &&
+                    out.inner == 1 && kron_hf_ok(la, lb);
+  int jfirst = 0, jlast = k;
+  if (fuse) {
+    const int64_t N = in.n;
+    const int64_t nmid = N >> (la + lb);
+    View d = out;
+    if (k > 2) {
+      d = packed_view(ctx.alloc((size_t)N * ncols * sizeof(float2)), FM_C64, 1, N, 1);
+      d.ld = N;
+    }
+    if (!ctx.dry) {
+      KronHFArgs h;
+      h.in = reinterpret_cast<const float2*>(in.p);
+      h.out = reinterpret_cast<float2*>(d.p);
+      h.in_ld = in.ld;
+      h.out_ld = d.ld;
+      h.nmid = nmid;
+      h.ntiles = ncols * nmid;
+      h.sa = nmid << lb;
+      h.dir = adj ? +1 : -1;
+      h.scale = fl->ortho ? (float)(1.0 / std::sqrt((double)fl->L)) : 1.f;
+      h.beta = k > 2 ? 0 : beta;
+      h.tw = tw_table<float>(ctx);
+      FM_TRY(kron_hf_launch(h, la, lb, ctx.st));
+    }
+    if (k == 2) {
+      ctx.used = mark;
+      return FM_OK;
+    }
+    src = d;
+    src.ostride = N;
+    jfirst = 1;
+    jlast = k - 1;
+  }
+  for (int j = jfirst; j < jlast; ++j) {
     const fm_op_s* f = A->kids[j];
     int64_t outer = in.outer, inner = in.inner;
     for (int l = 0; l < j; ++l) outer *= cur[l];
@@ -664,7 +708,7 @@ static fm_status exec_kron(const fm_op_s* A, bool adj, const View& in, const Vie
     s.inner = inner;
     s.n = cur[j];
     s.ostride = cur[j] * inner;
-    const bool last = j + 1 == k;
+    const bool last = j + 1 == jlast;
     View d;
     if (last) {
       // natural_out_dtype(A) == out.dt here: the caller promotes otherwise

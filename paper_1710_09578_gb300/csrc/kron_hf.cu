@@ -1,0 +1,127 @@
+// Fused mode products for Kron(H, ..., F): the Hadamard factor of the outermost axis and
+// the Fourier factor of the innermost (contiguous) axis applied in one pass.
+//
+// The mode products of a Kron operator commute (each acts on its own axis of the column
+// seen as a tensor, Sec. 3, Eq. (7)-style compositions), so the outer and inner factors can
+// be applied together.  A CTA takes the tile [2^LA][2^LB] of one column and one index of
+// the middle axes: rows are 2^LB contiguous complex64 elements, row a sits a * sa further
+// on.  The Fourier transform of the rows runs as the Stockham passes of the FFT tile kernel
+// (first pass straight from HBM, rows contiguous in shared memory), the Walsh-Hadamard
+// transform of the 2^LB columns as register rounds over the same shared-memory words
+// (vectors fastest), the last round straight to HBM.  One pass over HBM instead of two.
+#include "fft2.cuh"
+#include "fwht_rounds.cuh"
+#include "kron_hf.h"
+
+namespace fm {
+namespace {
+
+template <int THREADS, int EPT, int LA, int LB, int P>
+__device__ __forceinline__ void hrounds(float2 (&r)[EPT], float2* s, const KronHFArgs& a, float2* out) {
+  using Rd = WRound<LA, P>;
+  constexpr int R = 1 << Rd::RB;
+#pragma unroll
+  for (int q = 0; q < EPT / R; ++q) {
+    int v;
+    const int t0 = wgroup<THREADS, LB, Rd::SH, Rd::RB>(q, v);
+#pragma unroll
+    for (int k = 0; k < R; ++k) r[q * R + k] = s[wsp<LB>(t0 + (k << Rd::SH), v)];
+    wht_group<float2, R>(&r[q * R]);
+  }
+  if constexpr (P + 1 < Rd::NR) {
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < EPT / R; ++q) {
+      int v;
+      const int t0 = wgroup<THREADS, LB, Rd::SH, Rd::RB>(q, v);
+#pragma unroll
+      for (int k = 0; k < R; ++k) s[wsp<LB>(t0 + (k << Rd::SH), v)] = r[q * R + k];
+    }
+    __syncthreads();
+    hrounds<THREADS, EPT, LA, LB, P + 1>(r, s, a, out);
+  } else {
+    // last round: element (row t0 + k 2^SH, column v) straight to HBM
+#pragma unroll
+    for (int q = 0; q < EPT / R; ++q) {
+      int v;
+      const int t0 = wgroup<THREADS, LB, Rd::SH, Rd::RB>(q, v);
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        float2* p = out + (int64_t)(t0 + (k << Rd::SH)) * a.sa + v;
+        float2 y = cscale(r[q * R + k], a.scale);
+        if (a.beta) y = cadd(y, gld(p));
+        gst(p, y);
+      }
+    }
+  }
+}
+
+template <int LA, int LB>
+__global__ void __launch_bounds__(1 << (LA + LB - 4), 1) kron_hf_kernel(const __grid_constant__ KronHFArgs a) {
+  constexpr int THREADS = 1 << (LA + LB - 4), EPT = 16;
+  using S = Sched<LB>;
+  constexpr int LR0 = S::lr(0), LRL = S::lr(S::NR - 1);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* s = reinterpret_cast<float2*>(smem_raw);
+  const int64_t tile = blockIdx.x;
+  const int64_t col = tile / a.nmid, mid = tile % a.nmid;
+  const float2* in = a.in + col * a.in_ld + (mid << LB);
+  float2* out = a.out + col * a.out_ld + (mid << LB);
+  float2 r[EPT];
+  // Fourier along the rows: first pass straight from HBM (elements j + k M of row v)
+  {
+    constexpr int R = 1 << LR0, M = 1 << (LB - LR0);
+#pragma unroll
+    for (int q = 0; q < EPT / R; ++q) {
+      int j, v;
+      bfly2<false, THREADS, LB, LA, LR0>(q, j, v);
+      const float2* p = in + (int64_t)v * a.sa + j;
+#pragma unroll
+      for (int k = 0; k < R; ++k) r[q * R + k] = gld(p + k * M);
+    }
+  }
+  p2_run<float2, false, THREADS, EPT, LB, LA, 0, false>(r, s, a.dir, a.tw);
+  __syncthreads();
+  p2_write<float2, false, THREADS, EPT, LB, LA, LRL, LB - LRL>(r, s);  // natural order, rows contiguous
+  __syncthreads();
+  // Walsh-Hadamard along the columns (the 2^LB columns are the vectors, fastest)
+  hrounds<THREADS, EPT, LA, LB, 0>(r, s, a, out);
+}
+
+template <int LA, int LB>
+fm_status hf_start(const KronHFArgs& a, cudaStream_t st) {
+  constexpr int E = 1 << (LA + LB);
+  constexpr size_t smem = (size_t)(E + E / 16 + 1) * sizeof(float2);
+  auto kern = kron_hf_kernel<LA, LB>;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  static std::atomic<unsigned> attr_set{0};
+  if (dev < 32 && !(attr_set.load() & (1u << dev))) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) { set_error("kron_hf smem attribute: %s", cudaGetErrorString(e)); return FM_ERR_CUDA; }
+    attr_set.fetch_or(1u << dev);
+  }
+  if (a.ntiles == 0) return FM_OK;
+  if (a.ntiles > 0x7fffffffLL) { set_error("kron_hf: too many tiles"); return FM_ERR_UNSUPPORTED; }
+  kern<<<(unsigned)a.ntiles, 1 << (LA + LB - 4), smem, st>>>(a);
+  return after_launch("kron_hf_kernel");
+}
+
+}  // namespace
+
+bool kron_hf_ok(int la, int lb) { return la >= 4 && la <= 8 && lb >= 4 && lb <= 8 && la + lb >= 10 && la + lb <= 14; }
+
+fm_status kron_hf_launch(const KronHFArgs& a, int la, int lb, cudaStream_t st) {
+#define FM_HF(A, B) \
+  if (la == A && lb == B) return hf_start<A, B>(a, st);
+  FM_HF(4, 6) FM_HF(5, 5) FM_HF(6, 4)
+  FM_HF(4, 7) FM_HF(5, 6) FM_HF(6, 5) FM_HF(7, 4)
+  FM_HF(4, 8) FM_HF(5, 7) FM_HF(6, 6) FM_HF(7, 5) FM_HF(8, 4)
+  FM_HF(5, 8) FM_HF(6, 7) FM_HF(7, 6) FM_HF(8, 5)
+  FM_HF(6, 8) FM_HF(7, 7) FM_HF(8, 6)
+#undef FM_HF
+  set_error("kron_hf: no kernel for 2^%d x 2^%d", la, lb);
+  return FM_ERR_UNSUPPORTED;
+}
+
+}  // namespace fm

@@ -310,6 +310,27 @@ def test_kron_hadamard_strided_axis(fm, dt, la, lb):
     assert colerr(got, 2 * ref.apply(X.T.astype(np.complex128)).T) <= tol32(n)
 
 
+@pytest.mark.parametrize("la,mid,lb,ortho", [(4, 4, 6, 0), (6, 3, 4, 1), (7, 2, 6, 0), (5, 1, 5, 0), (8, 1, 6, 1),
+                                          (4, 1, 8, 0)])
+def test_kron_hadamard_fourier_fused(fm, la, mid, lb, ortho):
+    # Kron(H, middle, F) on complex64: the outer Hadamard and inner Fourier factors run as
+    # one fused pass (middle = 1: no middle factor, the pass writes the output directly)
+    c = I.cn(RNG, (mid,))
+    # middle factor: a circulant (power-of-two length) or a diagonal (any length), or none
+    pow2 = mid & (mid - 1) == 0
+    mk = ([fm.circulant(c)] if pow2 else [fm.diag(c)]) if mid > 1 else []
+    mr = ([O.Circulant(c)] if pow2 else [O.Diag(c)]) if mid > 1 else []
+    kids = [fm.hadamard(la)] + mk + [fm.fourier(1 << lb, ortho=bool(ortho))]
+    refs = [O.Hadamard(1 << la)] + mr + [O.Fourier(1 << lb, ortho=bool(ortho))]
+    A = fm.kron(*kids)
+    ref = O.Kron(*refs)
+    n = ref.cols
+    both(fm, A, ref, blk(3, n, np.complex64), blk(3, n, np.complex64), tol32(n))
+    X = blk(2, n, np.complex64)
+    got = fm.sum_(A, A).forward(gpu(X)).cpu().numpy()       # the second term accumulates
+    assert colerr(got, 2 * ref.apply(X.T).T) <= tol32(n)
+
+
 def test_kron_mixed_and_nested(fm):
     idx = np.array([0, 2, 5], dtype=np.int32)
     d = I.cn(RNG, (8,))
