@@ -37,8 +37,6 @@ fm_status device_tables(int device, DeviceTables** out) {
     DeviceTables& t = g_tabs[device];
     FM_CUDA(cudaMalloc(&t.tw32, sizeof(float2) * kTwMax));
     FM_CUDA(cudaMalloc(&t.tw64, sizeof(double2) * kTwMax));
-    FM_CUDA(cudaMalloc(&t.status, sizeof(int)));
-    FM_CUDA(cudaMemset(t.status, 0, sizeof(int)));
     FM_TRY(twiddle_launch(kTwMax, t.tw32, t.tw64, nullptr));
     FM_CUDA(cudaStreamSynchronize(nullptr));
     g_tab_ready[device] = true;

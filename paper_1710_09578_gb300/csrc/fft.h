@@ -1,4 +1,4 @@
-// Launch descriptor of the batched FFT engine (see fft.cu).
+// Launch descriptor of the batched FFT tile kernel (fft2.cuh).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -25,8 +25,6 @@ struct FftArgs {
   // transform
   int64_t L = 0;
   int logL = 0;
-  int nrad = 0;
-  int rad[16] = {0};
   int dir0 = -1;            // -1 forward (exp(-i...)), +1 inverse, for the first transform
   int conv = 0;             // 1: transform, x spectrum, inverse transform
   const C* spec = nullptr;  // length L (times spec_omod rows for per-row spectra)
@@ -35,21 +33,21 @@ struct FftArgs {
   const C* tw = nullptr;    // W_{kTwMax}^m table
   // geometry
   int64_t ncu = 0, ncols = 0, outer = 1, inner = 1;
-  int V = 1, logV = 0, vfast = 0;
+  int V = 1, logV = 0;
   // input view
   const void* in = nullptr;
   int64_t in_ld = 0, in_ostride = 0, in_tstride = 1;
   int64_t in_fmul = 1, in_fdiv = 1, in_fmod = 1, in_imod = 1;
   int in_mode = IO_C;
   int64_t Lin = 0;
-  int in_direct = 0, in_vcontig = 0;
+  int in_vcontig = 0;
   // output view
   void* out = nullptr;
   int64_t out_ld = 0, out_ostride = 0, out_tstride = 1;
   int64_t out_fmul = 1, out_fdiv = 1, out_fmod = 1, out_imod = 1;
   int out_mode = IO_C;
   int64_t Lout = 0;
-  int out_direct = 0, out_vcontig = 0;
+  int out_vcontig = 0;
   // twiddle index t * ((o*inner + i) / tw_div % tw_mod) of the two-pass plan
   int64_t tw_div = 1, tw_mod = 1;
   // pre ops (on load)

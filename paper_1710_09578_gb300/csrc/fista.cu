@@ -137,6 +137,88 @@ __device__ __forceinline__ void tile_fft(float2* s, int dir, const float2* tw) {
   __syncthreads();
 }
 
+// tile_fft(-1) whose first pass reads the residual u = P^T (P T y - b) instead of T y
+// (the MODE_RESID row mask of mask_rows applied to each element as it is read).
+template <int LOGL>
+__device__ __forceinline__ void tile_fft_resid(float2* s, const VState* vs, const float* b, const float2* tw) {
+  constexpr int LOGV = FGeo<LOGL>::LOGV, Nc = 1 << LOGL;
+  constexpr bool VF = FGeo<LOGL>::VF;
+  using S = Sched<LOGL>;
+  constexpr int LR0 = S::lr(0), LRL = S::lr(S::NR - 1), R = 1 << LR0, M = 1 << (LOGL - LR0);
+  float2 r[kFEpt];
+  p2_read<float2, VF, kFThreads, kFEpt, LOGL, LOGV, LR0>(r, s);
+#pragma unroll
+  for (int q = 0; q < kFEpt / R; ++q) {
+    int j, v;
+    bfly2<VF, kFThreads, LOGL, LOGV, LR0>(q, j, v);
+    const bool valid = vs[v].valid;
+    const int32_t* inv = vs[v].inv;
+    const float* bb = b + vs[v].b_off;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int kk = j + k * M;
+      float2 u = make_float2(0.f, 0.f);
+      if (valid && kk < (Nc >> 1)) {
+        const float2 z = r[q * R + k];
+        const int2 rr = *reinterpret_cast<const int2*>(inv + 2 * kk);
+        if (rr.x >= 0) u.x = z.x - bb[rr.x];
+        if (rr.y >= 0) u.y = z.y - bb[rr.y];
+      }
+      r[q * R + k] = u;
+    }
+  }
+  p2_run<float2, VF, kFThreads, kFEpt, LOGL, LOGV, 0, false>(r, s, -1, tw);
+  __syncthreads();
+  p2_write<float2, VF, kFThreads, kFEpt, LOGL, LOGV, LRL, LOGL - LRL>(r, s);
+  __syncthreads();
+}
+
+// tile_fft(+1) whose last pass, holding the gradient g = T^T u (unpacked pairs) in
+// registers, takes the FISTA step there: x_k = soft(y_k - g / L, lambda / L) and
+// y_{k+1} = x_k + beta (x_k - x_{k-1}) go to x and y, and pack(y_{k+1}) is what the pass
+// writes back to the tile for the next step.
+template <int LOGL>
+__device__ __forceinline__ void tile_ifft_update(float2* s, const VState* vs, float* x, float* y, float beta,
+                                                 const float2* tw) {
+  constexpr int LOGV = FGeo<LOGL>::LOGV, Nc = 1 << LOGL;
+  constexpr bool VF = FGeo<LOGL>::VF;
+  using S = Sched<LOGL>;
+  constexpr int LR0 = S::lr(0), LRL = S::lr(S::NR - 1), R = 1 << LRL, M = 1 << (LOGL - LRL);
+  float2 r[kFEpt];
+  p2_read<float2, VF, kFThreads, kFEpt, LOGL, LOGV, LR0>(r, s);
+  p2_run<float2, VF, kFThreads, kFEpt, LOGL, LOGV, 0, false>(r, s, +1, tw);
+#pragma unroll
+  for (int q = 0; q < kFEpt / R; ++q) {
+    int j, v;
+    bfly2<VF, kFThreads, LOGL, LOGV, LRL>(q, j, v);
+    const bool valid = vs[v].valid;
+    const int64_t xo = vs[v].x_off;
+    const float invL = vs[v].invL, thr = vs[v].thr;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int kk = j + k * M;
+      float2 ny = make_float2(0.f, 0.f);
+      if (valid && kk < (Nc >> 1)) {
+        const float2 g = r[q * R + k];
+        const int64_t o = xo + 2 * kk;
+        const float2 yv = ld_state(y + o);
+        const float2 xv = ld_state(x + o);
+        const float z0 = yv.x - g.x * invL, z1 = yv.y - g.y * invL;
+        const float m0 = fabsf(z0) - thr, m1 = fabsf(z1) - thr;
+        const float x0 = m0 > 0.f ? copysignf(m0, z0) : 0.f;
+        const float x1 = m1 > 0.f ? copysignf(m1, z1) : 0.f;
+        ny = make_float2(x0 + beta * (x0 - xv.x), x1 + beta * (x1 - xv.y));
+        st_state(x + o, make_float2(x0, x1));
+        st_state(y + o, ny);
+      }
+      r[q * R + k] = ny;
+    }
+  }
+  __syncthreads();
+  p2_write<float2, VF, kFThreads, kFEpt, LOGL, LOGV, LRL, LOGL - LRL>(r, s);
+  __syncthreads();
+}
+
 // Z <- pre-step( spectrum x post-step(Z) ) for every vector: see the file comment.
 template <int LOGL>
 __device__ void tile_spectral(float2* s, VState* vs, int adjoint, const float2* tw2) {
@@ -323,30 +405,13 @@ __device__ void fista_group(const FistaArgs& a, const FGroup& G, float2* s, VSta
     const double t = *s_t;
     const double tn = a.accel ? 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t)) : 1.0;
     const float beta = a.accel ? (float)((t - 1.0) / tn) : 0.f;
+    // A y_k, the residual (fused into the first pass of the next transform), A^T of it,
+    // and the step (fused into the last pass of the inverse transform)
     apply_T<LOGL>(s, vs, 0, a.tw, a.tw2);
-    mask_rows<LOGL, MODE_RESID>(s, vs, a.b, false);
-    apply_T<LOGL>(s, vs, 1, a.tw, a.tw2);
-    // update: g pairs at positions k < n/2; write x, y and the packed y_{k+1} for the next step
-    for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
-      const int v = q >> LOGL, kk = q & (Nc - 1);
-      float2* p = zaddr<LOGL>(s, kk, v);
-      float2 ny = make_float2(0.f, 0.f);
-      if (vs[v].valid && kk < (Nc >> 1)) {
-        const float2 g = *p;
-        const int64_t o = vs[v].x_off + 2 * kk;
-        const float2 yv = ld_state(a.y + o);
-        const float2 xv = ld_state(a.x + o);
-        const float invL = vs[v].invL, thr = vs[v].thr;
-        const float z0 = yv.x - g.x * invL, z1 = yv.y - g.y * invL;
-        const float m0 = fabsf(z0) - thr, m1 = fabsf(z1) - thr;
-        const float x0 = m0 > 0.f ? copysignf(m0, z0) : 0.f;
-        const float x1 = m1 > 0.f ? copysignf(m1, z1) : 0.f;
-        ny = make_float2(x0 + beta * (x0 - xv.x), x1 + beta * (x1 - xv.y));
-        st_state(a.x + o, make_float2(x0, x1));
-        st_state(a.y + o, ny);
-      }
-      *p = ny;
-    }
+    tile_fft_resid<LOGL>(s, vs, a.b, a.tw);
+    tile_spectral<LOGL>(s, vs, 1, a.tw2);
+    __syncthreads();
+    tile_ifft_update<LOGL>(s, vs, a.x, a.y, beta, a.tw);
     if (threadIdx.x == 0) *s_t = tn;
   }
   // ---- objective 1/2 ||A x - b||^2 + lambda ||x||_1 and status

@@ -74,7 +74,6 @@ constexpr int kTwMax = 1 << kTwLog;
 struct DeviceTables {
   float2* tw32 = nullptr;
   double2* tw64 = nullptr;
-  int* status = nullptr;  // 0, or an fm_status a kernel's bounded wait reported
 };
 fm_status device_tables(int device, DeviceTables** out);
 // The tables of `device` if they exist already, else nullptr (never allocates).

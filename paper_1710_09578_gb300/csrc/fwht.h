@@ -18,7 +18,6 @@ struct FwhtArgs {
   void* out = nullptr;
   int64_t out_ld = 0, out_ostride = 0, out_tstride = 1;
   int beta = 0;
-  int* err = nullptr;  // device status word set by bounded waits that run out
 };
 
 fm_status fwht_launch(FwhtArgs a, fm_dtype in_dt, cudaStream_t st);
