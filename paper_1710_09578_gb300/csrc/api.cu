@@ -112,7 +112,10 @@ static fm_status param_to_c128(const void* src, fm_dtype dt, int64_t n, int64_t 
 // Spectrum of the (embedding) circulant with first column c64 (length L), divided by L.
 static fm_status build_spectrum(fm_op_s* A, const double2* c64, int64_t L, cudaStream_t st) {
   A->L = L;
-  if (L > fft_max_tile<double>()) FM_TRY(make_big_plan(L, &A->big, st));
+  // Toeplitz operators (many small ones in a FISTA batch) keep the plan for long embeddings
+  // only; Circulant and Fourier get it from 2^11 for small FP64 problems
+  if (L > fft_max_tile<double>() || (A->kind == K_CIRCULANT && L >= kBigPlanMin))
+    FM_TRY(make_big_plan(L, &A->big, st));
   FM_CUDA(cudaMalloc(&A->spec64, sizeof(double2) * L));
   FM_CUDA(cudaMalloc(&A->spec32, sizeof(float2) * L));
   if (A->big.L) {
@@ -263,7 +266,7 @@ fm_status fm_fourier(int64_t n, int ortho, fm_op* out) {
   A->ortho = ortho ? 1 : 0;
   A->real = n == 1;
   fm_status s = FM_OK;
-  if (n > fft_max_tile<double>()) s = make_big_plan(n, &A->big, nullptr);
+  if (n >= kBigPlanMin) s = make_big_plan(n, &A->big, nullptr);
   if (s == FM_OK) {
     DeviceTables* t;
     s = device_tables(A->device, &t);

@@ -30,9 +30,11 @@ int ilog2_64(int64_t x) {
   return l;
 }
 
+// Transforms whose two-pass plan is used for full-size work (longer than one FP64 tile;
+// the shorter plans only serve small FP64 problems and keep their default split).
 void collect(fm_op_s* A, std::vector<fm_op_s*>& out) {
   if (!A) return;
-  if ((A->kind == K_FOURIER || A->kind == K_CIRCULANT || A->kind == K_TOEPLITZ) && A->big.L) {
+  if ((A->kind == K_FOURIER || A->kind == K_CIRCULANT || A->kind == K_TOEPLITZ) && A->big.L > 8192) {
     if (std::find(out.begin(), out.end(), A) == out.end()) out.push_back(A);
   }
   for (fm_op_s* k : A->kids) collect(k, out);

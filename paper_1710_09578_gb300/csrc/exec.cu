@@ -7,6 +7,7 @@
 // (mode products).  Inside a Product a Diag and a row selection next to an FFT-based
 // operator (Fourier, Circulant, Toeplitz) are fused into that operator's loads and stores:
 // the chain P . Diag(d) . C runs as one kernel, and its adjoint C^H . Diag(d)^H . P^H too.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -236,7 +237,13 @@ static fm_status run_fft(const FftJob& J, const Fused& F, const View& in, const 
     set_error("fft: input and output views differ in outer/inner");
     return FM_ERR_SHAPE;
   }
-  if (J.L <= fft_max_tile<T>()) {
+  // A small FP64 problem (a few columns of a transform of 2^11 .. 2^13) would occupy only a
+  // few CTAs as whole-vector tiles; its two-pass plan with one-warp tiles spreads the FP64
+  // work over many SMs.
+  const int64_t vec_single = std::max<int64_t>(1, 4096 / J.L);
+  const int64_t tiles_single = (ncu * in.outer * in.inner + vec_single - 1) / vec_single;
+  const bool small = sizeof(T) == 8 && J.big && J.big->L == J.L && J.L <= fft_max_tile<T>() && tiles_single < 64;
+  if (J.L <= fft_max_tile<T>() && !small) {
     if (ctx.dry) return FM_OK;
     FftArgs<T> a;
     a.L = J.L;
@@ -293,6 +300,7 @@ static fm_status run_fft(const FftJob& J, const Fused& F, const View& in, const 
   // pass A
   {
     FftArgs<T> a;
+    a.small = small ? 1 : 0;
     a.L = N1;
     a.dir0 = dirA;
     a.tw = tw_table<T>(ctx);
@@ -331,6 +339,7 @@ static fm_status run_fft(const FftJob& J, const Fused& F, const View& in, const 
   // pass B
   {
     FftArgs<T> a;
+    a.small = small ? 1 : 0;
     a.L = N2;
     a.tw = tw_table<T>(ctx);
     a.ncu = ncu;
@@ -382,6 +391,7 @@ static fm_status run_fft(const FftJob& J, const Fused& F, const View& in, const 
   // pass C
   {
     FftArgs<T> a;
+    a.small = small ? 1 : 0;
     a.L = N1;
     a.dir0 = +1;
     a.tw = tw_table<T>(ctx);

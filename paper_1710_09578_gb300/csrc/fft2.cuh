@@ -288,7 +288,7 @@ __device__ __forceinline__ void store_last(typename Cx<T>::t (&r)[EPT], const Ff
 // (24 warps per SM), 2 x 512 x 16; the 512 x 32 and FP64 tiles need their registers.
 template <typename T, int THREADS, int EPT, bool CONV>
 __host__ __device__ constexpr int fft2_min_blocks() {
-  return sizeof(T) != 4 ? 1 : (THREADS <= 256 ? 3 : (EPT <= 16 ? 2 : 1));
+  return sizeof(T) != 4 || THREADS < 256 ? 1 : (THREADS <= 256 ? 3 : (EPT <= 16 ? 2 : 1));
 }
 
 // The exchange buffer (none when a single radix pass does the whole transform in
@@ -366,10 +366,13 @@ __global__ void __launch_bounds__(THREADS, fft2_min_blocks<T, THREADS, EPT, CONV
   }
 }
 
-template <int LOGL, bool WIDE> struct TileCfg {
-  static constexpr int LOGE = WIDE ? (LOGL + 4 > 14 ? 14 : (LOGL + 4 < 12 ? 12 : LOGL + 4))
-                                   : (LOGL < 12 ? 12 : LOGL);
-  static constexpr int THREADS = LOGE <= 12 ? 256 : 512;
+// Tile shapes: 0 the default (2^12 elements, or one vector), 1 wide (16 vectors of a
+// strided view), 2 small (2^9 elements, one warp: many CTAs for small FP64 problems).
+template <int LOGL, int MODE> struct TileCfg {
+  static constexpr int LOGE = MODE == 1 ? (LOGL + 4 > 14 ? 14 : (LOGL + 4 < 12 ? 12 : LOGL + 4))
+                              : MODE == 2 ? (LOGL < 9 ? 9 : LOGL)
+                                          : (LOGL < 12 ? 12 : LOGL);
+  static constexpr int THREADS = MODE == 2 ? 32 : (LOGE <= 12 ? 256 : 512);
   static constexpr int EPT = (1 << LOGE) / THREADS;
 };
 
@@ -398,11 +401,11 @@ fm_status fft2_pick(const FftArgs<T>& a, bool simple, int64_t tiles, size_t smem
                 : fft2_start<T, LOGL, THREADS, EPT, VF, false, false>(a, tiles, smem, st);
 }
 
-template <typename T, int LOGL, bool WIDE>
+template <typename T, int LOGL, int MODE>
 fm_status fft2_launch_cfg(FftArgs<T> a, cudaStream_t st) {
   typedef typename Cx<T>::t C;
-  constexpr int THREADS = TileCfg<LOGL, WIDE>::THREADS;
-  constexpr int EPT = TileCfg<LOGL, WIDE>::EPT;
+  constexpr int THREADS = TileCfg<LOGL, MODE>::THREADS;
+  constexpr int EPT = TileCfg<LOGL, MODE>::EPT;
   constexpr int E = THREADS * EPT;
   constexpr int V = E >> LOGL;
   a.L = 1 << LOGL;
@@ -437,10 +440,13 @@ fm_status fft2_launch(FftArgs<T> a, cudaStream_t st) {
   // a wider tile for strided views of 2^9 .. 2^10 (FP32) or 2^9 (FP64): below 2^9 the
   // default tile already holds 16 vectors, above it E = 16 L exceeds shared memory
   constexpr int maxloge = sizeof(T) == 4 ? 14 : 13;
-  if constexpr (LOGL >= 9 && LOGL + 4 <= maxloge) {
-    if (a.inner >= 16) return fft2_launch_cfg<T, LOGL, true>(a, st);
+  if constexpr (sizeof(T) == 8 && LOGL >= 5 && LOGL <= 9) {
+    if (a.small) return fft2_launch_cfg<T, LOGL, 2>(a, st);
   }
-  return fft2_launch_cfg<T, LOGL, false>(a, st);
+  if constexpr (LOGL >= 9 && LOGL + 4 <= maxloge) {
+    if (a.inner >= 16) return fft2_launch_cfg<T, LOGL, 1>(a, st);
+  }
+  return fft2_launch_cfg<T, LOGL, 0>(a, st);
 }
 
 }  // namespace fm

@@ -85,7 +85,10 @@ enum OpKind {
   K_PRODUCT, K_SUM, K_BLKDIAG, K_KRON, K_HERMITIAN
 };
 
-// Twiddles and spectra for a length-L transform done in two passes (L = N1 * N2).
+// Twiddles and spectra for a length-L transform done in two passes (L = N1 * N2): every
+// transform longer than one tile, and (Fourier, Circulant) small FP64 problems of
+// 2^11 .. 2^13, spread over more CTAs.
+constexpr int64_t kBigPlanMin = 2048;
 struct BigPlan {
   int64_t L = 0, N1 = 0, N2 = 0;
   float2* tw32 = nullptr;   // W_L^m, m in [0, L)
