@@ -515,6 +515,41 @@ static fm_status exec_hadamard(const fm_op_s* A, const View& in, const View& out
     }
     return exec_pointwise(A, false, in, out, ncols, beta, ctx);
   }
+  if (A->log2n >= 17 && A->had_mode != FM_HAD_BF16 && A->had_mode != FM_HAD_BF16X2) {
+    // H_{2^(a+b)} = (H_{2^a} (x) I_{2^b}) (I_{2^a} (x) H_{2^b}): the low 14 index bits as
+    // contiguous blocks, then the top bits along the axis of stride 2^14 (in place in the
+    // output, or through a scratch column block when accumulating)
+    const int lb = 14, la = A->log2n - lb;
+    const int64_t nb = 1LL << lb, na = 1LL << la;
+    const fm_dtype td = in.dt == FM_I8 ? FM_I32 : in.dt;
+    View t = out;
+    const size_t mark = ctx.used;
+    if (beta || td != out.dt) t = temp_view(ctx, td, out, out.n, ncols);
+    fm_op_s hb, ha;  // the two factors (only their length and mode are read)
+    hb.kind = ha.kind = K_HADAMARD;
+    hb.had_mode = ha.had_mode = A->had_mode;
+    hb.log2n = lb;
+    ha.log2n = la;
+    View i1 = in, o1 = t;
+    i1.outer = in.outer * na;
+    i1.n = nb;
+    i1.ostride = nb * in.inner;
+    o1.outer = t.outer * na;
+    o1.n = nb;
+    o1.ostride = nb * t.inner;
+    if (in.outer > 1 && in.ostride != in.n * in.inner) {
+      set_error("Hadamard of length 2^%d on a view with a gap between outer blocks", A->log2n);
+      return FM_ERR_UNSUPPORTED;
+    }
+    FM_TRY(exec_hadamard(&hb, i1, o1, ncols, 0, ctx));
+    View i2 = t, o2 = out;
+    i2.n = o2.n = na;
+    i2.inner = nb * t.inner;
+    o2.inner = nb * out.inner;
+    FM_TRY(exec_hadamard(&ha, i2, o2, ncols, beta, ctx));
+    ctx.used = mark;
+    return FM_OK;
+  }
   FwhtArgs a;
   a.logL = A->log2n;
   a.ncols = ncols;

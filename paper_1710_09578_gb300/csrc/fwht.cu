@@ -32,6 +32,7 @@ template <typename Tin, typename W> __device__ __forceinline__ W wload(const Tin
 template <> __device__ __forceinline__ float wload<float, float>(const float* p) { return *p; }
 template <> __device__ __forceinline__ float2 wload<float2, float2>(const float2* p) { return *p; }
 template <> __device__ __forceinline__ int wload<int8_t, int>(const int8_t* p) { return (int)*p; }
+template <> __device__ __forceinline__ int wload<int, int>(const int* p) { return *p; }
 
 template <typename W, int R>
 __device__ __forceinline__ void wht_regs(W* x) {
@@ -335,6 +336,7 @@ fm_status fwht_launch(FwhtArgs a, fm_dtype in_dt, cudaStream_t st) {
     case FM_F32: return fwht_cfg<float, float, float, 512, 32>(a, st);
     case FM_C64: return fwht_cfg<float2, float2, float2, 512, 16>(a, st);
     case FM_I8: return fwht_cfg<int8_t, int, int, 512, 32>(a, st);
+    case FM_I32: return fwht_cfg<int, int, int, 512, 32>(a, st);  // second pass of long int8 columns
     default: break;
   }
   set_error("fwht: dtype %d not supported", (int)in_dt);

@@ -28,6 +28,7 @@ __device__ __forceinline__ int w_load(const int8_t* p) {
   asm volatile("ld.global.s8 %0, [%1];" : "=h"(v) : "l"(p));
   return (int)v;
 }
+__device__ __forceinline__ int w_load(const int* p) { return gld(p); }
 __device__ __forceinline__ float w_old(const float* p) { return gld(p); }
 __device__ __forceinline__ float2 w_old(const float2* p) { return gld(p); }
 __device__ __forceinline__ int w_old(const int* p) { return gld(p); }
@@ -191,6 +192,7 @@ fm_status fwht2_launch(const FwhtArgs& a, fm_dtype in_dt, cudaStream_t st) {
     case FM_F32: return fwht2_dispatch<float, float, float>(a, st);
     case FM_C64: return fwht2_dispatch<float2, float2, float2>(a, st);
     case FM_I8: return fwht2_dispatch<int8_t, int, int>(a, st);
+    case FM_I32: return fwht2_dispatch<int, int, int>(a, st);
     default: break;
   }
   set_error("fwht: dtype %d not supported", (int)in_dt);

@@ -190,6 +190,41 @@ def test_hadamard_long_columns_ld_and_sum(fm, log2n):
     assert np.array_equal(gi.astype(np.int64), O.Hadamard(n).apply(Xi[:, :n].T.astype(np.int64)).T)
 
 
+@pytest.mark.parametrize("log2n,dt", [(24, np.complex64), (22, np.complex128)])
+def test_fourier_and_circulant_largest(fm, log2n, dt):
+    # the largest lengths the constructors accept, through the two-pass plan
+    n = 1 << log2n
+    X = blk(1, n, dt)
+    tol = tol32(n) if dt == np.complex64 else 1e-10
+    got = fm.fourier(n).forward(gpu(X)).cpu().numpy()
+    assert colerr(got, O.Fourier(n).apply(X.T).T) <= tol
+    c = I.cn(RNG, (n,))
+    got = fm.circulant(c).backward(gpu(X)).cpu().numpy()
+    assert colerr(got, O.Circulant(c).apply(X.T, adjoint=True).T) <= tol
+
+
+@pytest.mark.parametrize("log2n,k", [(17, 2), (19, 1), (22, 1), (24, 1)])
+def test_hadamard_up_to_2p24(fm, log2n, k):
+    # lengths above one column tile run as two passes (low 14 index bits, then the rest)
+    n = 1 << log2n
+    X = blk(k, n, np.float32)
+    got = fm.hadamard(log2n).forward(gpu(X)).cpu().numpy()
+    assert colerr(got, O.Hadamard(n).apply(X.T.astype(np.float64)).T) <= tol32(n)
+
+
+def test_hadamard_long_int8_complex_and_sum(fm):
+    n = 1 << 20
+    Xi = RNG.integers(-128, 128, size=(2, n)).astype(np.int8)
+    gi = fm.hadamard(20, fm.FM_HAD_INT8).forward(gpu(Xi)).cpu().numpy()
+    assert gi.dtype == np.int32
+    assert np.array_equal(gi.astype(np.int64), O.Hadamard(n).apply(Xi.T.astype(np.int64)).T)
+    Xc = blk(2, 1 << 18, np.complex64)
+    both(fm, fm.hadamard(18), O.Hadamard(1 << 18), Xc, Xc, tol32(1 << 18))
+    X = blk(2, n, np.float32)
+    got = fm.sum_(fm.hadamard(20), fm.hadamard(20)).forward(gpu(X)).cpu().numpy()   # accumulation
+    assert colerr(got, 2 * O.Hadamard(n).apply(X.T.astype(np.float64)).T) <= tol32(n)
+
+
 def test_hadamard_bf16_workload_full(fm):
     xf, _ = I.hadamard_block()
     want = O.Hadamard(1 << 16).apply(xf.T.astype(np.float64)).T
