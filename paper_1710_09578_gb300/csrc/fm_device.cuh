@@ -13,6 +13,12 @@ template <> struct Cx<double> { typedef double2 t; };
 __device__ __forceinline__ float2 cmake(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ double2 cmake(double a, double b) { return make_double2(a, b); }
 
+// Programmatic dependent launch: pdl_wait() blocks until the previous grid of the stream has
+// completed with its writes visible (a no-op when the launch did not allow an early start);
+// pdl_launch_dependents() lets the next grid start once every CTA of this one has called it.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return cmake(a.x + b.x, a.y + b.y); }
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { return cmake(a.x - b.x, a.y - b.y); }
 template <typename C> __device__ __forceinline__ C cmul(C a, C b) {

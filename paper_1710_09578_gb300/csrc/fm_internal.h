@@ -46,6 +46,27 @@ inline fm_status after_launch(const char* what) {
   return FM_OK;
 }
 
+// Launch that lets the kernel's CTAs become resident while the previous kernel of the stream
+// drains its last wave (programmatic dependent launch).  A kernel launched this way executes
+// pdl_wait() (fm_device.cuh) before its first global-memory access, which returns once the
+// previous grid has completed and its writes are visible; launched without the attribute,
+// pdl_wait() returns at once.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // ------------------------------------------------------------------ dtypes
 inline bool is_complex(fm_dtype d) { return d == FM_C64 || d == FM_C128; }
 inline bool is_double(fm_dtype d) { return d == FM_F64 || d == FM_C128; }

@@ -216,6 +216,8 @@ __global__ void __launch_bounds__(512, 2) fwht_long_kernel(const Tin* __restrict
   const int t = threadIdx.x;
   const Tin* x = in + col * in_ld + 8 * t;
   W r[32];
+  pdl_launch_dependents();
+  pdl_wait();
 
   // round A: e = c + 8 t + 4096 q, registers hold bits {0,1,2} (c) and {12,13} (q)
 #pragma unroll
@@ -279,12 +281,14 @@ static fm_status fwht_long(const FwhtArgs& a, cudaStream_t st) {
   W* out = reinterpret_cast<W*>(a.out);
   const int64_t blocks = a.ncols << logC;
   if (blocks == 0) return FM_OK;
+  cudaError_t e;
   switch (logC) {
-    case 0: fwht_long_kernel<Tin, W, 1><<<(unsigned)blocks, 512, 0, st>>>(in, a.in_ld, out, a.out_ld, a.beta); break;
-    case 1: fwht_long_kernel<Tin, W, 2><<<(unsigned)blocks, 512, 0, st>>>(in, a.in_ld, out, a.out_ld, a.beta); break;
-    case 2: fwht_long_kernel<Tin, W, 4><<<(unsigned)blocks, 512, 0, st>>>(in, a.in_ld, out, a.out_ld, a.beta); break;
+    case 0: e = launch_pdl(fwht_long_kernel<Tin, W, 1>, dim3((unsigned)blocks), dim3(512), 0, st, in, a.in_ld, out, a.out_ld, a.beta); break;
+    case 1: e = launch_pdl(fwht_long_kernel<Tin, W, 2>, dim3((unsigned)blocks), dim3(512), 0, st, in, a.in_ld, out, a.out_ld, a.beta); break;
+    case 2: e = launch_pdl(fwht_long_kernel<Tin, W, 4>, dim3((unsigned)blocks), dim3(512), 0, st, in, a.in_ld, out, a.out_ld, a.beta); break;
     default: set_error("fwht_long: unsupported length"); return FM_ERR_UNSUPPORTED;
   }
+  if (e != cudaSuccess) { set_error("launch of fwht_long_kernel: %s", cudaGetErrorString(e)); return FM_ERR_CUDA; }
   return after_launch("fwht_long_kernel");
 }
 
