@@ -312,6 +312,7 @@ __global__ void __launch_bounds__(THREADS, fft2_min_blocks<T, THREADS, EPT, CONV
   VecInfo* vinfo = reinterpret_cast<VecInfo*>(smem_raw + fft2_vinfo_offset<C, LOGL>(E));
   const int64_t g0 = (int64_t)blockIdx.x * V;
   const int64_t nvec = a.ncu * a.outer * a.inner;
+  pdl_launch_dependents();
 
   for (int v = threadIdx.x; v < V; v += THREADS) {
     VecInfo vi;
@@ -338,6 +339,7 @@ __global__ void __launch_bounds__(THREADS, fft2_min_blocks<T, THREADS, EPT, CONV
     }
     vinfo[v] = vi;
   }
+  pdl_wait();
   __syncthreads();
 
   constexpr int LR0 = S::lr(0);
@@ -387,8 +389,7 @@ fm_status fft2_start(const FftArgs<T>& a, int64_t tiles, size_t smem, cudaStream
     if (e != cudaSuccess) { set_error("fft smem attribute: %s", cudaGetErrorString(e)); return FM_ERR_CUDA; }
     attr_bytes[dev].store(smem);
   }
-  kern<<<(unsigned)tiles, THREADS, smem, st>>>(a);
-  return after_launch("fft2_kernel");
+  return pdl_go("fft2_kernel", kern, dim3((unsigned)tiles), dim3(THREADS), smem, st, a);
 }
 
 template <typename T, int LOGL, int THREADS, int EPT, bool VF>

@@ -66,6 +66,17 @@ inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kern, args...);
 }
+template <typename... KArgs, typename... Args>
+inline fm_status pdl_go(const char* what, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                        cudaStream_t st, Args... args) {
+  cudaError_t e = launch_pdl(kern, grid, block, smem, st, args...);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    set_error("launch of %s failed: %s", what, cudaGetErrorString(e));
+    return FM_ERR_CUDA;
+  }
+  return after_launch(what);
+}
 
 // ------------------------------------------------------------------ dtypes
 inline bool is_complex(fm_dtype d) { return d == FM_C64 || d == FM_C128; }

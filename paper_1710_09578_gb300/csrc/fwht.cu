@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(THREADS) fwht_tile_kernel(const __grid_constan
   const int64_t g0 = tile * V;
   const int64_t nvec = a.ncols * a.outer * a.inner;
   const int vfast = V >= 16;
+  pdl_launch_dependents();
 
   for (int v = threadIdx.x; v < V; v += THREADS) {
     WVec vi;
@@ -124,6 +125,7 @@ __global__ void __launch_bounds__(THREADS) fwht_tile_kernel(const __grid_constan
     }
     vinfo[v] = vi;
   }
+  pdl_wait();
   __syncthreads();
 
   const Tin* in = reinterpret_cast<const Tin*>(a.in);
@@ -281,15 +283,16 @@ static fm_status fwht_long(const FwhtArgs& a, cudaStream_t st) {
   W* out = reinterpret_cast<W*>(a.out);
   const int64_t blocks = a.ncols << logC;
   if (blocks == 0) return FM_OK;
-  cudaError_t e;
+  const char* nm = "fwht_long_kernel";
+  const dim3 grid((unsigned)blocks), blk(512);
   switch (logC) {
-    case 0: e = launch_pdl(fwht_long_kernel<Tin, W, 1>, dim3((unsigned)blocks), dim3(512), 0, st, in, a.in_ld, out, a.out_ld, a.beta); break;
-    case 1: e = launch_pdl(fwht_long_kernel<Tin, W, 2>, dim3((unsigned)blocks), dim3(512), 0, st, in, a.in_ld, out, a.out_ld, a.beta); break;
-    case 2: e = launch_pdl(fwht_long_kernel<Tin, W, 4>, dim3((unsigned)blocks), dim3(512), 0, st, in, a.in_ld, out, a.out_ld, a.beta); break;
-    default: set_error("fwht_long: unsupported length"); return FM_ERR_UNSUPPORTED;
+    case 0: return pdl_go(nm, fwht_long_kernel<Tin, W, 1>, grid, blk, 0, st, in, a.in_ld, out, a.out_ld, a.beta);
+    case 1: return pdl_go(nm, fwht_long_kernel<Tin, W, 2>, grid, blk, 0, st, in, a.in_ld, out, a.out_ld, a.beta);
+    case 2: return pdl_go(nm, fwht_long_kernel<Tin, W, 4>, grid, blk, 0, st, in, a.in_ld, out, a.out_ld, a.beta);
+    default: break;
   }
-  if (e != cudaSuccess) { set_error("launch of fwht_long_kernel: %s", cudaGetErrorString(e)); return FM_ERR_CUDA; }
-  return after_launch("fwht_long_kernel");
+  set_error("fwht_long: unsupported length");
+  return FM_ERR_UNSUPPORTED;
 }
 
 // Plain contiguous column blocks of length 2^14..2^16 with 16-byte aligned columns.
@@ -327,8 +330,7 @@ static fm_status fwht_cfg(FwhtArgs a, cudaStream_t st) {
     attr_bytes[dev].store(smem);
   }
   if (blocks == 0) return FM_OK;
-  kern<<<(unsigned)blocks, THREADS, smem, st>>>(a);
-  return after_launch("fwht_tile_kernel");
+  return pdl_go("fwht_tile_kernel", kern, dim3((unsigned)blocks), dim3(THREADS), smem, st, a);
 }
 
 fm_status fwht_launch(FwhtArgs a, fm_dtype in_dt, cudaStream_t st) {

@@ -82,6 +82,7 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 3 : 1) fwht2_kernel(
   WVec2* vinfo = reinterpret_cast<WVec2*>(smem_raw + voff);
   const int64_t g0 = (int64_t)blockIdx.x * V;
   const int64_t nvec = a.ncols * a.outer * a.inner;
+  pdl_launch_dependents();
   for (int v = threadIdx.x; v < V; v += THREADS) {
     WVec2 vi;
     const int64_t g = g0 + v;
@@ -96,6 +97,7 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 3 : 1) fwht2_kernel(
     }
     vinfo[v] = vi;
   }
+  pdl_wait();
   __syncthreads();
 
   // round 0 straight from HBM
@@ -156,8 +158,7 @@ fm_status fwht2_start(const FwhtArgs& a, cudaStream_t st) {
     if (e != cudaSuccess) { set_error("fwht smem attribute: %s", cudaGetErrorString(e)); return FM_ERR_CUDA; }
     attr_bytes[dev].store(smem);
   }
-  kern<<<(unsigned)tiles, THREADS, smem, st>>>(a);
-  return after_launch("fwht2_kernel");
+  return pdl_go("fwht2_kernel", kern, dim3((unsigned)tiles), dim3(THREADS), smem, st, a);
 }
 
 template <typename Tin, typename W, typename Tout>

@@ -57,6 +57,8 @@ __global__ void __launch_bounds__(512) fwht_mma_kernel(const float* __restrict__
   const int64_t col = blockIdx.x / nparts;
   const float* x = in + col * in_ld;
   float* y = out + col * out_ld + (int64_t)part * Lp;
+  pdl_launch_dependents();
+  pdl_wait();
   for (int i = threadIdx.x; i < Lp; i += blockDim.x) {
     float acc = 0.f;
     for (int sb = 0; sb < nparts; ++sb) {
@@ -224,6 +226,8 @@ __global__ void __launch_bounds__(kTcThreads, kTcMinBlocks)
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int g = lane >> 2, tq = lane & 3;
   const float* x = in + col * in_ld;
+  pdl_launch_dependents();
+  pdl_wait();
 
   // the C blocks combined with row `part` of H_C, 16 bytes per thread and load
 #pragma unroll 1
@@ -348,8 +352,8 @@ static fm_status fwht_tc_launch(const FwhtArgs& a, cudaStream_t st) {
     }
     attr_set[ci].fetch_or(1u << dev);
   }
-  kern<<<(unsigned)(a.ncols * C), kTcThreads, smem, st>>>(in, a.in_ld, out, a.out_ld, a.beta);
-  return after_launch("fwht_tc_kernel");
+  return pdl_go("fwht_tc_kernel", kern, dim3((unsigned)(a.ncols * C)), dim3(kTcThreads), smem, st, in, a.in_ld, out,
+                a.out_ld, a.beta);
 }
 
 fm_status fwht_mma_launch(FwhtArgs a, int split, cudaStream_t st) {
@@ -379,8 +383,8 @@ fm_status fwht_mma_launch(FwhtArgs a, int split, cudaStream_t st) {
   const float* in = reinterpret_cast<const float*>(a.in);
   float* out = reinterpret_cast<float*>(a.out);
   auto kern = split ? k1 : k0;
-  kern<<<(unsigned)(a.ncols * C), 512, smem, st>>>(in, a.in_ld, out, a.out_ld, a.beta, logLp, C);
-  return after_launch("fwht_mma_kernel");
+  return pdl_go("fwht_mma_kernel", kern, dim3((unsigned)(a.ncols * C)), dim3(512), smem, st, in, a.in_ld, out,
+                a.out_ld, a.beta, logLp, C);
 }
 
 }  // namespace fm

@@ -68,6 +68,8 @@ __global__ void __launch_bounds__(1 << (LA + LB - 4), 1) kron_hf_kernel(const __
   const float2* in = a.in + col * a.in_ld + (mid << LB);
   float2* out = a.out + col * a.out_ld + (mid << LB);
   float2 r[EPT];
+  pdl_launch_dependents();
+  pdl_wait();
   // Fourier along the rows: first pass straight from HBM (elements j + k M of row v)
   {
     constexpr int R = 1 << LR0, M = 1 << (LB - LR0);
@@ -103,8 +105,7 @@ fm_status hf_start(const KronHFArgs& a, cudaStream_t st) {
   }
   if (a.ntiles == 0) return FM_OK;
   if (a.ntiles > 0x7fffffffLL) { set_error("kron_hf: too many tiles"); return FM_ERR_UNSUPPORTED; }
-  kern<<<(unsigned)a.ntiles, 1 << (LA + LB - 4), smem, st>>>(a);
-  return after_launch("kron_hf_kernel");
+  return pdl_go("kron_hf_kernel", kern, dim3((unsigned)a.ntiles), dim3(1 << (LA + LB - 4)), smem, st, a);
 }
 
 }  // namespace

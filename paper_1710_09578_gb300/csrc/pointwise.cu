@@ -11,6 +11,8 @@ template <typename T>
 __global__ void pointwise_kernel(const __grid_constant__ PwArgs a) {
   typedef typename Cx<T>::t C;
   const int64_t total = a.ncols * a.outer * a.n_out * a.inner;
+  pdl_launch_dependents();
+  pdl_wait();
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e % a.inner;
@@ -50,8 +52,7 @@ static fm_status pw_go(const PwArgs& a, cudaStream_t st) {
   if (total == 0) return FM_OK;
   int64_t blocks = (total + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
-  pointwise_kernel<T><<<(unsigned)blocks, 256, 0, st>>>(a);
-  return after_launch("pointwise_kernel");
+  return pdl_go("pointwise_kernel", pointwise_kernel<T>, dim3((unsigned)blocks), dim3(256), 0, st, a);
 }
 
 fm_status pointwise_launch(const PwArgs& a, bool dbl, cudaStream_t st) {
@@ -62,6 +63,8 @@ fm_status pointwise_launch(const PwArgs& a, bool dbl, cudaStream_t st) {
 __global__ void i32_copy_kernel(const int* in, int64_t in_ld, int* out, int64_t out_ld, int64_t n,
                                 int64_t ncols, int beta) {
   const int64_t total = n * ncols;
+  pdl_launch_dependents();
+  pdl_wait();
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c = e / n, t = e % n;
@@ -77,8 +80,8 @@ fm_status i32_copy_launch(const int* in, int64_t in_ld, int* out, int64_t out_ld
   if (total == 0) return FM_OK;
   int64_t blocks = (total + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
-  i32_copy_kernel<<<(unsigned)blocks, 256, 0, st>>>(in, in_ld, out, out_ld, n, ncols, beta);
-  return after_launch("i32_copy_kernel");
+  return pdl_go("i32_copy_kernel", i32_copy_kernel, dim3((unsigned)blocks), dim3(256), 0, st, in, in_ld, out, out_ld,
+                n, ncols, beta);
 }
 
 // W_N^m = exp(-2 pi i m / N) for m in [0, N), computed in FP64 with sincospi.
