@@ -238,7 +238,7 @@ static fm_status run_fft(const FftJob& J, const Fused& F, const View& in, const 
     return FM_ERR_SHAPE;
   }
   // A small FP64 problem (a few columns of a transform of 2^11 .. 2^13) would occupy only a
-  // few CTAs as whole-vector tiles; its two-pass plan with one-warp tiles spreads the FP64
+  // few CTAs as whole-vector tiles; its two-pass plan with small tiles spreads the FP64
   // work over many SMs.
   const int64_t vec_single = std::max<int64_t>(1, 4096 / J.L);
   const int64_t tiles_single = (ncu * in.outer * in.inner + vec_single - 1) / vec_single;

@@ -34,7 +34,7 @@ struct FftArgs {
   // geometry
   int64_t ncu = 0, ncols = 0, outer = 1, inner = 1;
   int V = 1, logV = 0;
-  int small = 0;            // 1: one-warp tiles (passes of a small two-pass FP64 problem)
+  int small = 0;            // 1: small tiles (passes of a small two-pass FP64 problem)
   // input view
   const void* in = nullptr;
   int64_t in_ld = 0, in_ostride = 0, in_tstride = 1;

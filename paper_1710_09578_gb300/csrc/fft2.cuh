@@ -38,11 +38,28 @@ __host__ __device__ constexpr int sched_nr(int logl) {
   return n;
 }
 
-template <int LOGL>
+// Tiles whose threads hold fewer than 16 elements cap the radix at 2^LMAX (the EPT elements
+// of a thread must hold whole butterflies): ceil(LOGL / LMAX) passes, larger radices first.
+__host__ __device__ constexpr int sched_cap_nr(int logl, int lmax) { return (logl + lmax - 1) / lmax; }
+__host__ __device__ constexpr int sched_cap_lr(int logl, int lmax, int p) {
+  return p < sched_cap_nr(logl, lmax)
+             ? logl / sched_cap_nr(logl, lmax) + (p < logl % sched_cap_nr(logl, lmax) ? 1 : 0)
+             : 0;
+}
+// log2 of the largest radix a thread with EPT elements can hold (at most 16).
+template <int EPT>
+__host__ __device__ constexpr int ept_lmax() {
+  return EPT >= 16 ? 4 : (EPT >= 8 ? 3 : (EPT >= 4 ? 2 : 1));
+}
+
+template <int LOGL, int LMAX = 4>
 struct Sched {
   static_assert(LOGL >= 1 && LOGL <= 14, "transform length 2^1 .. 2^14 per tile");
-  static constexpr int NR = sched_nr(LOGL);
-  __host__ __device__ static constexpr int lr(int p) { return sched_lr(LOGL, p); }
+  static_assert(LMAX >= 1 && LMAX <= 4, "radix 2 .. 16");
+  static constexpr int NR = LMAX >= 4 ? sched_nr(LOGL) : sched_cap_nr(LOGL, LMAX);
+  __host__ __device__ static constexpr int lr(int p) {
+    return LMAX >= 4 ? sched_lr(LOGL, p) : sched_cap_lr(LOGL, LMAX, p);
+  }
   // log2 Ns before forward pass q (radices in order) and before inverse pass q (reversed)
   __host__ __device__ static constexpr int ns_fwd(int q) {
     int s = 0;
@@ -177,7 +194,7 @@ __device__ __forceinline__ void p2_compute(C (&r)[EPT], int dir, const C* __rest
 
 template <typename C, bool VF, int THREADS, int EPT, int LOGL, int LOGV, int P, bool INV>
 __device__ __forceinline__ void p2_run(C (&r)[EPT], C* s, int dir, const C* tw) {
-  using S = Sched<LOGL>;
+  using S = Sched<LOGL, ept_lmax<EPT>()>;
   if constexpr (P < S::NR) {
     constexpr int LR = INV ? S::lr(S::NR - 1 - P) : S::lr(P);
     constexpr int LOGNS = INV ? S::ns_inv(P) : S::ns_fwd(P);
@@ -293,9 +310,9 @@ __host__ __device__ constexpr int fft2_min_blocks() {
 
 // The exchange buffer (none when a single radix pass does the whole transform in
 // registers), then the per-vector table.
-template <typename C, int LOGL>
+template <typename C, int LOGL, int EPT>
 __host__ __device__ constexpr size_t fft2_vinfo_offset(int E) {
-  return Sched<LOGL>::NR > 1 ? fft_vinfo_offset<C>(E) : 0;
+  return Sched<LOGL, ept_lmax<EPT>()>::NR > 1 ? fft_vinfo_offset<C>(E) : 0;
 }
 
 // SIMPLE: no fused operation on either side (complex in and out, natural index, no map,
@@ -306,10 +323,10 @@ __global__ void __launch_bounds__(THREADS, fft2_min_blocks<T, THREADS, EPT, CONV
     fft2_kernel(const __grid_constant__ FftArgs<T> a) {
   typedef typename Cx<T>::t C;
   constexpr int E = THREADS * EPT, LOGE = ilog2c(E), LOGV = LOGE - LOGL, V = 1 << LOGV;
-  using S = Sched<LOGL>;
+  using S = Sched<LOGL, ept_lmax<EPT>()>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
-  VecInfo* vinfo = reinterpret_cast<VecInfo*>(smem_raw + fft2_vinfo_offset<C, LOGL>(E));
+  VecInfo* vinfo = reinterpret_cast<VecInfo*>(smem_raw + fft2_vinfo_offset<C, LOGL, EPT>(E));
   const int64_t g0 = (int64_t)blockIdx.x * V;
   const int64_t nvec = a.ncu * a.outer * a.inner;
   pdl_launch_dependents();
@@ -369,12 +386,13 @@ __global__ void __launch_bounds__(THREADS, fft2_min_blocks<T, THREADS, EPT, CONV
 }
 
 // Tile shapes: 0 the default (2^12 elements, or one vector), 1 wide (16 vectors of a
-// strided view), 2 small (2^9 elements, one warp: many CTAs for small FP64 problems).
+// strided view), 2 small (2^9 elements, four warps of 4 elements per thread: many CTAs for
+// small FP64 problems, with a warp on every SM sub-partition's FP64 unit).
 template <int LOGL, int MODE> struct TileCfg {
   static constexpr int LOGE = MODE == 1 ? (LOGL + 4 > 14 ? 14 : (LOGL + 4 < 12 ? 12 : LOGL + 4))
                               : MODE == 2 ? (LOGL < 9 ? 9 : LOGL)
                                           : (LOGL < 12 ? 12 : LOGL);
-  static constexpr int THREADS = MODE == 2 ? 32 : (LOGE <= 12 ? 256 : 512);
+  static constexpr int THREADS = MODE == 2 ? 128 : (LOGE <= 12 ? 256 : 512);
   static constexpr int EPT = (1 << LOGE) / THREADS;
 };
 
@@ -426,7 +444,7 @@ fm_status fft2_launch_cfg(FftArgs<T> a, cudaStream_t st) {
   }
   a.in_vcontig = (a.inner > 1 || a.in_ostride == 1) ? 1 : 0;
   a.out_vcontig = (a.inner > 1 || a.out_ostride == 1) ? 1 : 0;
-  const size_t smem = fft2_vinfo_offset<C, LOGL>(E) + (size_t)V * sizeof(VecInfo);
+  const size_t smem = fft2_vinfo_offset<C, LOGL, EPT>(E) + (size_t)V * sizeof(VecInfo);
   const bool simple = a.in_mode == IO_C && a.out_mode == IO_C && !a.pre_map && !a.pre_dc && !a.pre_dr &&
                       !a.pre_tw && !a.post_tw && !a.post_dc && !a.post_dr && !a.post_map && a.scale == (T)1 &&
                       !a.beta && a.in_fmul == 1 && a.in_fmod == 1 && a.out_fmul == 1 && a.out_fmod == 1;

@@ -127,7 +127,7 @@ template <int LOGL>
 __device__ __forceinline__ void tile_fft(float2* s, int dir, const float2* tw) {
   constexpr int LOGV = FGeo<LOGL>::LOGV;
   constexpr bool VF = FGeo<LOGL>::VF;
-  using S = Sched<LOGL>;
+  using S = Sched<LOGL, ept_lmax<kFEpt>()>;
   constexpr int LR0 = S::lr(0), LRL = S::lr(S::NR - 1);
   float2 r[kFEpt];
   p2_read<float2, VF, kFThreads, kFEpt, LOGL, LOGV, LR0>(r, s);
@@ -143,7 +143,7 @@ template <int LOGL>
 __device__ __forceinline__ void tile_fft_resid(float2* s, const VState* vs, const float* b, const float2* tw) {
   constexpr int LOGV = FGeo<LOGL>::LOGV, Nc = 1 << LOGL;
   constexpr bool VF = FGeo<LOGL>::VF;
-  using S = Sched<LOGL>;
+  using S = Sched<LOGL, ept_lmax<kFEpt>()>;
   constexpr int LR0 = S::lr(0), LRL = S::lr(S::NR - 1), R = 1 << LR0, M = 1 << (LOGL - LR0);
   float2 r[kFEpt];
   p2_read<float2, VF, kFThreads, kFEpt, LOGL, LOGV, LR0>(r, s);
@@ -182,7 +182,7 @@ __device__ __forceinline__ void tile_ifft_update(float2* s, const VState* vs, fl
                                                  const float2* tw) {
   constexpr int LOGV = FGeo<LOGL>::LOGV, Nc = 1 << LOGL;
   constexpr bool VF = FGeo<LOGL>::VF;
-  using S = Sched<LOGL>;
+  using S = Sched<LOGL, ept_lmax<kFEpt>()>;
   constexpr int LR0 = S::lr(0), LRL = S::lr(S::NR - 1), R = 1 << LRL, M = 1 << (LOGL - LRL);
   float2 r[kFEpt];
   p2_read<float2, VF, kFThreads, kFEpt, LOGL, LOGV, LR0>(r, s);
