@@ -181,8 +181,8 @@ __global__ void __launch_bounds__(THREADS) fwht_tile_kernel(const __grid_constan
 // register rounds over bit groups {0,1,2,12,13}, {3..7} and {8..11} with two shared-memory
 // exchanges in between.  The first round loads straight from HBM with one 32-byte vector
 // load per block and register group (all C blocks combined with row r of H_C as they
-// arrive); the last round stores straight to HBM (128 contiguous bytes per warp and
-// instruction).  Shared-memory word of element e: bits 3-4 XOR bits 8-9 and bit 2 XOR bit 5,
+// arrive); the last round stores straight to HBM (an aligned pair of elements per thread,
+// 256 contiguous bytes per warp and instruction).  Shared-memory word of element e: bits 3-4 XOR bits 8-9 and bit 2 XOR bit 5,
 // which keeps 16-byte groups intact and makes the round-A 16-byte stores and the round-B
 // and round-C accesses bank-conflict free.
 __device__ __forceinline__ int lswz(int e) { return e ^ (((e >> 8) & 3) << 3) ^ (((e >> 5) & 1) << 2); }
@@ -190,6 +190,9 @@ __device__ __forceinline__ int lswz(int e) { return e ^ (((e >> 8) & 3) << 3) ^ 
 template <typename W> struct Vec4;
 template <> struct Vec4<float> { typedef float4 t; };
 template <> struct Vec4<int> { typedef int4 t; };
+template <typename W> struct Vec2;
+template <> struct Vec2<float> { typedef float2 t; };
+template <> struct Vec2<int> { typedef int2 t; };
 
 __device__ __forceinline__ void ld8(const float* p, float (&v)[8]) {
   asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -204,6 +207,8 @@ __device__ __forceinline__ void ld8(const int8_t* p, int (&v)[8]) {
     v[4 + i] = (int)(int8_t)((u.y >> (8 * i)) & 0xff);
   }
 }
+__device__ __forceinline__ float2 make_vec2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ int2 make_vec2(int a, int b) { return make_int2(a, b); }
 __device__ __forceinline__ float4 make_vec4(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
 __device__ __forceinline__ int4 make_vec4(int a, int b, int c, int d) { return make_int4(a, b, c, d); }
 
@@ -255,24 +260,32 @@ __global__ void __launch_bounds__(512, 2) fwht_long_kernel(const Tin* __restrict
   }
   __syncthreads();
 
-  // round C: e = l + 256 m + 4096 h with l = t & 255, h = 2 (t >> 8) + g; registers hold
-  // bits 8..11 (m) for g = 0, 1
+  // round C: e = c + 2 l + 256 m + 4096 h with l = t & 127, h = t >> 7; registers hold bits
+  // 8..11 (m) for both values of bit 0 (c, carried untransformed), so that every
+  // shared-memory read and HBM write moves an aligned pair of elements
   {
-    const int l = t & 255, h0 = 2 * (t >> 8);
+    typedef typename Vec2<W>::t V2;
+    const int l = t & 127, h = t >> 7;
+    const int e0 = 2 * l + 4096 * h;
 #pragma unroll
-    for (int g = 0; g < 2; ++g)
-#pragma unroll
-      for (int m = 0; m < 16; ++m) r[16 * g + m] = s[lswz(l + 256 * m + 4096 * (h0 + g))];
+    for (int m = 0; m < 16; ++m) {
+      const V2 v = *reinterpret_cast<const V2*>(&s[lswz(e0 + 256 * m)]);
+      r[m] = v.x;
+      r[16 + m] = v.y;
+    }
     wht_regs<W, 16>(r);
     wht_regs<W, 16>(r + 16);
-    W* y = out + col * out_ld + (int64_t)part * LP;
+    W* y = out + col * out_ld + (int64_t)part * LP + e0;
 #pragma unroll
-    for (int g = 0; g < 2; ++g)
-#pragma unroll
-      for (int m = 0; m < 16; ++m) {
-        W* p = y + l + 256 * m + 4096 * (h0 + g);
-        *p = beta ? *p + r[16 * g + m] : r[16 * g + m];
+    for (int m = 0; m < 16; ++m) {
+      V2* p = reinterpret_cast<V2*>(y + 256 * m);
+      V2 v = make_vec2(r[m], r[16 + m]);
+      if (beta) {
+        const V2 o = *p;
+        v = make_vec2(v.x + o.x, v.y + o.y);
       }
+      *p = v;
+    }
   }
 }
 
