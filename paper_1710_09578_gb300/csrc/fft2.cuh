@@ -386,10 +386,10 @@ __global__ void __launch_bounds__(THREADS, fft2_min_blocks<T, THREADS, EPT, CONV
 }
 
 // Tile shapes: 0 the default (2^12 elements, or one vector), 1 wide (16 vectors of a
-// strided view), 2 small (2^9 elements, four warps of 4 elements per thread: many CTAs for
+// strided view, 8 for 2^10 so that two CTAs of 16 elements per thread share an SM), 2 small (2^9 elements, four warps of 4 elements per thread: many CTAs for
 // small FP64 problems, with a warp on every SM sub-partition's FP64 unit).
 template <int LOGL, int MODE> struct TileCfg {
-  static constexpr int LOGE = MODE == 1 ? (LOGL + 4 > 14 ? 14 : (LOGL + 4 < 12 ? 12 : LOGL + 4))
+  static constexpr int LOGE = MODE == 1 ? (LOGL + 4 > 13 ? 13 : (LOGL + 4 < 12 ? 12 : LOGL + 4))
                               : MODE == 2 ? (LOGL < 9 ? 9 : LOGL)
                                           : (LOGL < 12 ? 12 : LOGL);
   static constexpr int THREADS = MODE == 2 ? 128 : (LOGE <= 12 ? 256 : 512);
