@@ -291,6 +291,31 @@ def test_product_pdc_fused(fm, n):
     both(fm, A, ref, blk(3, n, np.complex64), blk(3, n // 4, np.complex64), tol32(n))
 
 
+def test_back_to_back_dependent_launches(fm):
+    # Every kernel starts early and waits for its predecessor on the stream before touching
+    # memory: long chains of dependent calls with no host synchronisation must give the
+    # composed result.
+    n, k = 1 << 16, 8
+    X = blk(k, n, np.float32)
+    H = fm.hadamard(16)
+    bufs = [gpu(X), torch.empty((k, n), dtype=torch.float32, device=DEV)]
+    for i in range(6):
+        H.forward(bufs[i % 2], out=bufs[(i + 1) % 2])
+    got = bufs[0].cpu().numpy().astype(np.float64)
+    assert colerr(got, X.astype(np.float64) * float(n) ** 3) <= 6 * tol32(n)
+    # forward, adjoint, forward of a three-pass operator, again without synchronising
+    m = 1 << 18
+    c, d, idx = _pdc(m, m // 4, 11)
+    A = fm.product(fm.partial(idx, m), fm.diag(d), fm.circulant(c))
+    ref = O.Product(O.Partial(idx, m), O.Diag(d), O.Circulant(c))
+    Xc = blk(2, m, np.complex64)
+    W = A.forward(A.backward(A.forward(gpu(Xc)))).cpu().numpy()
+    want = ref.apply(ref.apply(ref.apply(Xc.T), adjoint=True)).T
+    # a race (a pass reading its predecessor's output early) gives O(1) errors; the bound
+    # leaves room for the rounding of three applies amplified by C's spread of |spectrum|
+    assert colerr(W, want) <= 10 * tol32(m)
+
+
 def test_cs_operator_workload_full(fm):
     # Phi = P Diag(d) C at N = 2^18, M = N/4, 64 complex64 columns
     c, d, idx, X, Y, G = I.cs_operator()
