@@ -199,13 +199,25 @@ __device__ __forceinline__ void ld8(const float* p, float (&v)[8]) {
                : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
                : "l"(p));
 }
+// Byte i of w sign-extended to 32 bits in one byte permute: selector nibble 0 copies byte
+// i, nibbles 1-3 (msb set) replicate its sign bit.
+template <int I>
+__device__ __forceinline__ int sext8(unsigned w) {
+  constexpr unsigned sel = I | ((8u | I) << 4) | ((8u | I) << 8) | ((8u | I) << 12);
+  unsigned d;
+  asm("prmt.b32 %0, %1, 0, %2;" : "=r"(d) : "r"(w), "n"(sel));
+  return (int)d;
+}
 __device__ __forceinline__ void ld8(const int8_t* p, int (&v)[8]) {
   const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    v[i] = (int)(int8_t)((u.x >> (8 * i)) & 0xff);
-    v[4 + i] = (int)(int8_t)((u.y >> (8 * i)) & 0xff);
-  }
+  v[0] = sext8<0>(u.x);
+  v[1] = sext8<1>(u.x);
+  v[2] = sext8<2>(u.x);
+  v[3] = sext8<3>(u.x);
+  v[4] = sext8<0>(u.y);
+  v[5] = sext8<1>(u.y);
+  v[6] = sext8<2>(u.y);
+  v[7] = sext8<3>(u.y);
 }
 __device__ __forceinline__ float2 make_vec2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ int2 make_vec2(int a, int b) { return make_int2(a, b); }
