@@ -342,23 +342,44 @@ def _gbs_loop(fn, nbytes, steps, flush, stream, torch):
     return nbytes * steps / (sum(ts) / 1e3) / 1e9
 
 
+def _b2b_rotating(fns, nbytes, reps, stream, torch):
+    """GB/s of algorithmic bytes for back-to-back calls cycling through buffer sets that
+    together exceed L2 (no flush, no host gap), the way the headline step is timed."""
+    for f in fns:
+        f()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(reps):
+        fns[i % len(fns)]()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return nbytes * reps / (e0.elapsed_time(e1) / 1e3) / 1e9
+
+
 def measure_rows(fm, torch, dev, stream, flush, xi, cpu_sample=True):
     """GB/s of the other hot-path rows (forward + adjoint, algorithmic bytes)."""
     rows = {}
-    # int8 -> int32 Hadamard (exact)
-    Xi = torch.from_numpy(xi).to(dev)
+    # int8 -> int32 Hadamard (exact); four sets of X (16 MiB) and Y (64 MiB) for the
+    # back-to-back figure
+    Xi = [torch.from_numpy(xi).to(dev) for _ in range(4)]
     Ai = fm.hadamard(LOG2N, fm.FM_HAD_INT8)
-    Yi = torch.empty((NCOLS, N), dtype=torch.int32, device=dev)
-    rows["hadamard_int8_fwd"] = {"GB/s": _gbs_loop(lambda: Ai.forward(Xi, out=Yi), N * NCOLS * 5, 200, flush,
-                                                   stream, torch)}
+    Yi = [torch.empty((NCOLS, N), dtype=torch.int32, device=dev) for _ in range(4)]
+    rows["hadamard_int8_fwd"] = {
+        "GB/s": _gbs_loop(lambda: Ai.forward(Xi[0], out=Yi[0]), N * NCOLS * 5, 200, flush, stream, torch),
+        "GB/s_back_to_back_rotating": _b2b_rotating(
+            [lambda k=k: Ai.forward(Xi[k], out=Yi[k]) for k in range(4)], N * NCOLS * 5, 400, stream, torch)}
     del Xi, Yi
     # BF16 tensor-core Hadamard (FP32 in and out, BF16 products with FP32 accumulation) and its
     # split hi + lo form
-    Xf = torch.from_numpy(I.hadamard_block()[0]).to(dev)
-    Yf = torch.empty_like(Xf)
+    Xf = [torch.from_numpy(I.hadamard_block()[0]).to(dev) for _ in range(4)]
+    Yf = [torch.empty_like(Xf[0]) for _ in range(4)]
     for name, mode in (("hadamard_bf16_fwd", fm.FM_HAD_BF16), ("hadamard_bf16x2_fwd", fm.FM_HAD_BF16X2)):
         Ab = fm.hadamard(LOG2N, mode)
-        rows[name] = {"GB/s": _gbs_loop(lambda: Ab.forward(Xf, out=Yf), APPLY_BYTES, 200, flush, stream, torch)}
+        rows[name] = {
+            "GB/s": _gbs_loop(lambda: Ab.forward(Xf[0], out=Yf[0]), APPLY_BYTES, 200, flush, stream, torch),
+            "GB/s_back_to_back_rotating": _b2b_rotating(
+                [lambda k=k: Ab.forward(Xf[k], out=Yf[k]) for k in range(4)], APPLY_BYTES, 400, stream, torch)}
     del Xf, Yf
     # compressed-sensing operator Phi = P Diag(d) C, N = 2^18, 64 complex64 columns
     c, d, idx, X, Yc, _ = I.cs_operator()

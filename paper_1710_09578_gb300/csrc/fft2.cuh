@@ -301,11 +301,13 @@ __device__ __forceinline__ void store_last(typename Cx<T>::t (&r)[EPT], const Ff
   }
 }
 
-// Resident CTAs per SM the register allocation is held to, for FP32 tiles: 3 x 256 threads
-// (24 warps per SM), 2 x 512 x 16; the 512 x 32 and FP64 tiles need their registers.
+// Resident CTAs per SM the register allocation is held to, for FP32 tiles: 4 x 256 threads
+// (32 warps per SM; at most a few registers spill), 3 x 256 for the convolution tiles (their
+// spectrum product needs more registers), 2 x 512 x 16; the 512 x 32 and FP64 tiles need
+// their registers.
 template <typename T, int THREADS, int EPT, bool CONV>
 __host__ __device__ constexpr int fft2_min_blocks() {
-  return sizeof(T) != 4 || THREADS < 256 ? 1 : (THREADS <= 256 ? 3 : (EPT <= 16 ? 2 : 1));
+  return sizeof(T) != 4 || THREADS < 256 ? 1 : (THREADS <= 256 ? (CONV ? 3 : 4) : (EPT <= 16 ? 2 : 1));
 }
 
 // The exchange buffer (none when a single radix pass does the whole transform in
