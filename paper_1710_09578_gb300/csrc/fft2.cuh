@@ -302,12 +302,15 @@ __device__ __forceinline__ void store_last(typename Cx<T>::t (&r)[EPT], const Ff
 }
 
 // Resident CTAs per SM the register allocation is held to, for FP32 tiles: 4 x 256 threads
-// (32 warps per SM; at most a few registers spill), 3 x 256 for the convolution tiles (their
-// spectrum product needs more registers), 2 x 512 x 16; the 512 x 32 and FP64 tiles need
-// their registers.
-template <typename T, int THREADS, int EPT, bool CONV>
+// (32 warps per SM; at most a few registers spill), 3 x 256 for the convolution tiles of
+// 2^5, 2^6 and 2^9 (radix-8 passes with two butterflies per thread, whose spectrum product
+// would spill tens of bytes at 64 registers), 2 x 512 x 16; the 512 x 32 and FP64 tiles
+// need their registers.
+template <typename T, int LOGL, int THREADS, int EPT, bool CONV>
 __host__ __device__ constexpr int fft2_min_blocks() {
-  return sizeof(T) != 4 || THREADS < 256 ? 1 : (THREADS <= 256 ? (CONV ? 3 : 4) : (EPT <= 16 ? 2 : 1));
+  return sizeof(T) != 4 || THREADS < 256
+             ? 1
+             : (THREADS <= 256 ? (CONV && (LOGL == 5 || LOGL == 6 || LOGL == 9) ? 3 : 4) : (EPT <= 16 ? 2 : 1));
 }
 
 // The exchange buffer (none when a single radix pass does the whole transform in
@@ -321,7 +324,7 @@ __host__ __device__ constexpr size_t fft2_vinfo_offset(int E) {
 // diagonal, twiddle, scale or accumulation): loads and stores are a base plus a stride.
 // CONV: transform, spectrum product, inverse transform (circulant and Toeplitz products).
 template <typename T, int LOGL, int THREADS, int EPT, bool VF, bool SIMPLE, bool CONV>
-__global__ void __launch_bounds__(THREADS, fft2_min_blocks<T, THREADS, EPT, CONV>())
+__global__ void __launch_bounds__(THREADS, fft2_min_blocks<T, LOGL, THREADS, EPT, CONV>())
     fft2_kernel(const __grid_constant__ FftArgs<T> a) {
   typedef typename Cx<T>::t C;
   constexpr int E = THREADS * EPT, LOGE = ilog2c(E), LOGV = LOGE - LOGL, V = 1 << LOGV;
