@@ -39,8 +39,8 @@ STEP_BYTES = 2 * APPLY_BYTES               # forward + adjoint
 METRIC = "fwd+adjoint apply GB/s vs HBM peak; batched FISTA solves/s at 1e-4 rel err"
 WORKLOAD = "Sylvester Hadamard n=2^16, 256 FP32 columns, forward + adjoint"
 # DRAM bytes of one fwht_long_kernel launch on this workload, from the ncu capture
-# summarised in profiles/fwht_long_kernel_hadamard_2p16x256.md (read 67.14 MB + write 23.67 MB).
-NCU_TRAFFIC = 90802688
+# summarised in profiles/fwht_long_kernel_hadamard_2p16x256.md (read 67.14 MB + write 22.87 MB).
+NCU_TRAFFIC = 90012160
 
 
 def _peaks():
