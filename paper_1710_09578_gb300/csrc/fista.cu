@@ -234,7 +234,8 @@ __device__ void tile_spectral(float2* s, VState* vs, int adjoint, const float2* 
     // E = (Zk + conj Zm)/2, O = (Zk - conj Zm)/(2i)
     const float2 E = make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y));
     const float2 O = make_float2(0.5f * (Zk.y + Zm.y), -0.5f * (Zk.x - Zm.x));
-    const float2 wk = tw2[k << tsh], wkp = tw2[kp << tsh];
+    // W_{2Nc}^(Nc - k) = -conj(W_{2Nc}^k): one table read for the pair
+    const float2 wk = tw2[k << tsh], wkp = make_float2(-wk.x, wk.y);
     const float2 Wk = cadd(E, cmul(wk, O));
     const float2 Wkp = cadd(cconj(E), cmul(wkp, cconj(O)));
     float2 sk = vs[v].spec[k], skp = vs[v].spec[kp];
