@@ -89,6 +89,14 @@ def test_circulant_real_pairs(fm, n):
     both(fm, fm.circulant(c), O.Circulant(c), blk(5, n, np.float32), blk(5, n, np.float32), tol32(n))
 
 
+@pytest.mark.parametrize("n,k", [(2048, 3), (8192, 2), (8192, 80)])
+def test_circulant_c128_two_pass_small_tiles(fm, n, k):
+    # complex128 transforms of 2^11 .. 2^13 on a few columns run the two-pass plan on
+    # four-warp tiles with radix-4 passes; with 64 columns or more, whole-vector tiles
+    c = I.cn(RNG, (n,))
+    both(fm, fm.circulant(c), O.Circulant(c), blk(k, n, np.complex128), blk(k, n, np.complex128), 1e-12)
+
+
 def test_circulant_tiny_workload_c128(fm):
     # Circulant N=4096 with K=16 complex128 columns, against the dense definition
     c, X, Y = I.circulant_tiny()
