@@ -135,7 +135,7 @@ fm_status fm_calibrate(fm_op A, int64_t ncols, fm_dtype dt, void* stream, fm_tun
     const int64_t L = leaf->big.L;
     const int lg = ilog2_64(L);
     std::vector<int64_t> cand;
-    for (int e : {lg / 2, 6, 5, 7, lg - 13, lg - 12}) {
+    for (int e : {lg / 2, lg / 2 - 1, lg / 2 + 1, 6, 5, 7, lg - 13, lg - 12}) {
       const int64_t n1 = (int64_t)1 << std::max(e, 0);
       if (split_ok(L, n1) && std::find(cand.begin(), cand.end(), n1) == cand.end()) cand.push_back(n1);
     }
