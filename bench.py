@@ -275,10 +275,11 @@ def main():
 
     # ---- end to end through the public API with host buffers: every step copies its input
     # from pinned host memory, runs forward + adjoint and copies the result back.  Steps
-    # alternate between two streams with their own device and host buffers, so the copies
-    # of one step overlap the transforms of the other (the Hadamard operator keeps no
-    # workspace, so the two streams share nothing on the device).
-    NE = 2
+    # rotate over three streams with their own device and host buffers, so the copies of
+    # one step overlap the transforms and copies of the others (the Hadamard operator keeps
+    # no workspace, so the streams share nothing on the device); with two streams a step's
+    # upload waits for the download two steps back on the same stream.
+    NE = 3
     e2e_streams = [torch.cuda.Stream(dev) for _ in range(NE)]
     Xe = [torch.empty_like(Xs[0]) for _ in range(NE)]
     Ye = [torch.empty_like(Xs[0]) for _ in range(NE)]
