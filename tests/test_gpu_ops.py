@@ -324,6 +324,45 @@ def test_back_to_back_dependent_launches(fm):
     assert colerr(W, want) <= 10 * tol32(m)
 
 
+def test_graph_capture_replays_chained_launches(fm):
+    # the chained launches captured into a CUDA graph (programmatic edges) and replayed give
+    # the eager result bit for bit, and the oracle's within tolerance
+    n = 1 << 14
+    c, d, idx = _pdc(n, n // 4, 12)
+    A = fm.product(fm.partial(idx, n), fm.diag(d), fm.circulant(c))
+    ref = O.Product(O.Partial(idx, n), O.Diag(d), O.Circulant(c))
+    H = fm.hadamard(15)
+    X = gpu(blk(4, n, np.complex64))
+    Xh = gpu(blk(4, 1 << 15, np.float32))
+    Y = torch.empty((4, n // 4), dtype=torch.complex64, device=DEV)
+    Z = torch.empty_like(X)
+    Hy = torch.empty_like(Xh)
+    Hz = torch.empty_like(Xh)
+    A.reserve(4, torch.complex64)
+
+    def run():
+        A.forward(X, out=Y)
+        A.backward(Y, out=Z)
+        H.forward(Xh, out=Hy)
+        H.forward(Hy, out=Hz)
+
+    run()
+    torch.cuda.synchronize()
+    Z0, Hz0 = Z.clone(), Hz.clone()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        run()
+    Z.zero_()
+    Hz.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(Z, Z0) and torch.equal(Hz, Hz0)
+    Xn = X.cpu().numpy()
+    want = ref.apply(ref.apply(Xn.T), adjoint=True).T
+    assert colerr(Z.cpu().numpy(), want) <= 10 * tol32(n)  # two applies, C's spread of |spectrum|
+    assert colerr(Hz.cpu().numpy(), Xh.cpu().numpy().astype(np.float64) * float(1 << 15)) <= 2 * tol32(1 << 15)
+
+
 def test_cs_operator_workload_full(fm):
     # Phi = P Diag(d) C at N = 2^18, M = N/4, 64 complex64 columns
     c, d, idx, X, Y, G = I.cs_operator()
