@@ -194,8 +194,11 @@ template <typename W> struct Vec2;
 template <> struct Vec2<float> { typedef float2 t; };
 template <> struct Vec2<int> { typedef int2 t; };
 
+// Coherent global loads (never the read-only .nc path): with programmatic dependent launch
+// the kernel is resident while the previous grid still writes its input, and a
+// non-coherent load may be served before the griddepcontrol.wait that orders them.
 __device__ __forceinline__ void ld8(const float* p, float (&v)[8]) {
-  asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+  asm volatile("ld.global.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
                : "l"(p));
 }
@@ -209,7 +212,8 @@ __device__ __forceinline__ int sext8(unsigned w) {
   return (int)d;
 }
 __device__ __forceinline__ void ld8(const int8_t* p, int (&v)[8]) {
-  const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+  uint2 u;
+  asm volatile("ld.global.v2.u32 {%0, %1}, [%2];" : "=r"(u.x), "=r"(u.y) : "l"(p));
   v[0] = sext8<0>(u.x);
   v[1] = sext8<1>(u.x);
   v[2] = sext8<2>(u.x);
@@ -225,8 +229,8 @@ __device__ __forceinline__ float4 make_vec4(float a, float b, float c, float d) 
 __device__ __forceinline__ int4 make_vec4(int a, int b, int c, int d) { return make_int4(a, b, c, d); }
 
 template <typename Tin, typename W, int C>
-__global__ void __launch_bounds__(512, 2) fwht_long_kernel(const Tin* __restrict__ in, int64_t in_ld,
-                                                           W* __restrict__ out, int64_t out_ld, int beta) {
+__global__ void __launch_bounds__(512, 2) fwht_long_kernel(const Tin* in, int64_t in_ld, W* out, int64_t out_ld,
+                                                           int beta) {
   typedef typename Vec4<W>::t V4;
   constexpr int LP = 1 << 14;
   __shared__ __align__(32) W s[LP];

@@ -48,8 +48,8 @@ __device__ __forceinline__ float hdigit(int row, int col, int id) {
 }
 
 template <int SPLIT>
-__global__ void __launch_bounds__(512) fwht_mma_kernel(const float* __restrict__ in, int64_t in_ld,
-                                                       float* __restrict__ out, int64_t out_ld, int beta,
+__global__ void __launch_bounds__(512) fwht_mma_kernel(const float* in, int64_t in_ld,
+                                                       float* out, int64_t out_ld, int beta,
                                                        int logLp, int nparts) {
   extern __shared__ __align__(16) float s[];
   const int Lp = 1 << logLp;
@@ -214,11 +214,19 @@ __device__ __forceinline__ void frag_two_digits(float (&z)[8], const float (&x)[
 }
 
 // threads per CTA and resident CTAs per SM of the long-column kernel
+// Coherent 16-byte global load (not the read-only .nc path, which may be served before the
+// griddepcontrol.wait that orders this kernel after the grid writing its input).
+__device__ __forceinline__ float4 ld4(const float* p) {
+  float4 r;
+  asm volatile("ld.global.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w) : "l"(p));
+  return r;
+}
+
 constexpr int kTcThreads = 512, kTcMinBlocks = 2;
 
 template <int SPLIT, int C>
 __global__ void __launch_bounds__(kTcThreads, kTcMinBlocks)
-    fwht_tc_kernel(const float* __restrict__ in, int64_t in_ld, float* __restrict__ out, int64_t out_ld, int beta) {
+    fwht_tc_kernel(const float* in, int64_t in_ld, float* out, int64_t out_ld, int beta) {
   constexpr int LP = 1 << 14, NT = kTcThreads, NW = NT / 32, NCH = LP / 4 / NT;
   extern __shared__ __align__(16) float s[];
   const int part = (int)(blockIdx.x % C);
@@ -237,7 +245,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcMinBlocks)
     for (int i = 0; i < 2; ++i)
 #pragma unroll
       for (int sb = 0; sb < C; ++sb)
-        v[i][sb] = __ldg(reinterpret_cast<const float4*>(x + (int64_t)sb * LP + 4 * (t + NT * (i0 + i))));
+        v[i][sb] = ld4(x + (int64_t)sb * LP + 4 * (t + NT * (i0 + i)));
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
       float4 acc = v[i][0];
