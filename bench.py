@@ -39,8 +39,8 @@ STEP_BYTES = 2 * APPLY_BYTES               # forward + adjoint
 METRIC = "fwd+adjoint apply GB/s vs HBM peak; batched FISTA solves/s at 1e-4 rel err"
 WORKLOAD = "Sylvester Hadamard n=2^16, 256 FP32 columns, forward + adjoint"
 # DRAM bytes of one fwht_long_kernel launch on this workload, from the ncu capture
-# summarised in profiles/fwht_long_kernel_hadamard_2p16x256.md (read 67.14 MB + write 22.87 MB).
-NCU_TRAFFIC = 90012160
+# summarised in profiles/fwht_long_kernel_hadamard_2p16x256.md (read 67.13 MB + write 23.01 MB).
+NCU_TRAFFIC = 90139392
 
 
 def _peaks():
@@ -228,17 +228,23 @@ def main():
     Xh = torch.from_numpy(xf).pin_memory()
     # NSETS rotating buffer sets (X, Y, Z: 3 x 64 MiB each): the sets touched by the three
     # previous steps (576 MiB) exceed L2, so every step starts from cold data without a flush
-    # and the steps run back to back (no host gap between the events and the kernels)
+    # and the steps run back to back (no host gap between the events and the kernels).
+    # Steps are independent column blocks: even steps run on the launching stream and odd
+    # steps on a second stream (even and odd steps use disjoint sets), so the kernels of
+    # one stream fill the last, partly empty wave of the other's.  The roofline below is
+    # still the per-launch figure of a single stream.
     NSETS = 4
     Xs = [Xh.to(dev) for _ in range(NSETS)]
     Ys = [torch.empty_like(Xs[0]) for _ in range(NSETS)]
     Zs = [torch.empty_like(Xs[0]) for _ in range(NSETS)]
     A = fm.hadamard(LOG2N)
+    stream_b = torch.cuda.Stream(dev)
 
     def step(i):
         k = i % NSETS
-        A.forward(Xs[k], out=Ys[k])
-        A.backward(Ys[k], out=Zs[k])
+        with torch.cuda.stream(stream_b if i % 2 else stream):
+            A.forward(Xs[k], out=Ys[k])
+            A.backward(Ys[k], out=Zs[k])
 
     for i in range(max(3, args.warmup)):
         step(i)
@@ -248,10 +254,14 @@ def main():
     torch.cuda.synchronize()
     l0 = fm.launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    eb = torch.cuda.Event()
     with Clocks(local) as clk:
         e0.record(stream)
+        stream_b.wait_event(e0)
         for i in range(args.steps):
             step(i)
+        eb.record(stream_b)
+        stream.wait_event(eb)
         e1.record(stream)
         torch.cuda.synchronize()
     launches = fm.launch_count() - l0
@@ -317,6 +327,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": N, "columns": NCOLS, "bytes_per_step": STEP_BYTES,
                        "l2": "inputs larger than L2: 4 rotating sets of X, Y, Z (768 MiB), steps back to back",
+                       "streams": "independent steps alternate over 2 streams; roofline from 1 stream",
                        "parallelism": f"replicas x{world}"},
             "clocks": clk.summary(),
             "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": N * NCOLS * 4,
