@@ -16,6 +16,9 @@ __device__ __forceinline__ double2 cmake(double a, double b) { return make_doubl
 // Programmatic dependent launch: pdl_wait() blocks until the previous grid of the stream has
 // completed with its writes visible (a no-op when the launch did not allow an early start);
 // pdl_launch_dependents() lets the next grid start once every CTA of this one has called it.
+// A kernel launched this way reads data that the previous grid writes only through coherent
+// loads (ld.global): a read-only .nc load (ld.global.nc, __ldg, or one the compiler derives
+// from a const __restrict__ pointer) may be served before the wait.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
