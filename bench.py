@@ -150,7 +150,8 @@ def reference_arm(args, world, rank):
     line = {"impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "n": N, "columns": NCOLS},
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n": N, "columns": NCOLS, "bytes_per_step": STEP_BYTES,
+                                            "parallelism": "oracle on one host core"},
             "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
                              "sample": f"{cols} of {NCOLS} columns per step, FP64 numpy butterflies"},
             "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
