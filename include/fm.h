@@ -21,7 +21,10 @@
  *   caller.
  * Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *   stream).  All device work is enqueued on it; no call synchronises the
- *   device unless stated.
+ *   device unless stated.  Transform kernels are launched with programmatic
+ *   dependent launch: they may become resident while the previous kernel of the
+ *   stream finishes, but touch memory only after it has completed, so stream
+ *   order is kept as usual (also inside captured CUDA graphs).
  * Errors.  Every call returns fm_status.  Argument checks run before any
  *   launch and leave outputs untouched.  Asynchronous CUDA failures surface as
  *   FM_ERR_CUDA from a later call.  fm_last_error() gives a one-line message
