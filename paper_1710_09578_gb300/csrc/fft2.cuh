@@ -245,10 +245,16 @@ __device__ __forceinline__ void load_first(typename Cx<T>::t (&r)[EPT], const Ff
       const bool unit = a.in_tstride == 1;
       const int64_t step = unit ? M : (int64_t)M * a.in_tstride;
       const C* in = reinterpret_cast<const C*>(a.in) + vi.in_off + (unit ? j : (int64_t)j * a.in_tstride);
+      if (vi.in_off >= 0 && j + (R - 1) * M < a.Lin) {
+        // the whole butterfly lies inside the vector: no per-element checks
 #pragma unroll
-      for (int k = 0; k < R; ++k) {
-        const bool ok = vi.in_off >= 0 && j + k * M < a.Lin;
-        r[q * R + k] = ok ? gld(unit ? in + k * M : in + k * step) : cmake((T)0, (T)0);
+        for (int k = 0; k < R; ++k) r[q * R + k] = gld(unit ? in + k * M : in + k * step);
+      } else {
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+          const bool ok = vi.in_off >= 0 && j + k * M < a.Lin;
+          r[q * R + k] = ok ? gld(unit ? in + k * M : in + k * step) : cmake((T)0, (T)0);
+        }
       }
     } else {
       // fused loads in runs of at most 8 (registers: each run keeps its row indices live)
@@ -286,9 +292,14 @@ __device__ __forceinline__ void store_last(typename Cx<T>::t (&r)[EPT], const Ff
       const bool unit = a.out_tstride == 1;
       const int64_t step = unit ? M : (int64_t)M * a.out_tstride;
       C* out = reinterpret_cast<C*>(a.out) + vi.out_off + (unit ? j : (int64_t)j * a.out_tstride);
+      if (vi.out_off >= 0 && j + (R - 1) * M < a.Lout) {
 #pragma unroll
-      for (int k = 0; k < R; ++k) {
-        if (vi.out_off >= 0 && j + k * M < a.Lout) gst(unit ? out + k * M : out + k * step, r[q * R + k]);
+        for (int k = 0; k < R; ++k) gst(unit ? out + k * M : out + k * step, r[q * R + k]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+          if (vi.out_off >= 0 && j + k * M < a.Lout) gst(unit ? out + k * M : out + k * step, r[q * R + k]);
+        }
       }
     } else {
       constexpr int H = R > 8 ? 8 : R;
