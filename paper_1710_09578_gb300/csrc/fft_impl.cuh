@@ -55,35 +55,42 @@ __device__ __forceinline__ void fft_load_bfly(const FftArgs<T>& a, const VecInfo
   }
   const int fmul = (int)a.in_fmul, Lin = (int)a.Lin, ts = (int)a.in_tstride;
   const int n0 = j * fmul + vi.in_n2, dn = M * fmul;
-  int src[R];
-  if (a.pre_map) {
-#pragma unroll
-    for (int k = 0; k < R; ++k) {
-      const int n = n0 + k * dn;
-      src[k] = n < Lin ? gld(a.pre_map + n) : -1;
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < R; ++k) {
-      const int n = n0 + k * dn;
-      src[k] = n < Lin ? n : -1;
-    }
-  }
-  if (a.in_mode == IO_C) {
+  if (a.in_mode == IO_C && !a.pre_map && n0 + (R - 1) * dn < Lin) {
+    // complex input, no row map, the whole butterfly inside the vector: no per-element checks
     const C* p = reinterpret_cast<const C*>(a.in) + vi.in_off;
 #pragma unroll
-    for (int k = 0; k < R; ++k) x[k] = src[k] >= 0 ? gld(p + src[k] * ts) : zero;
+    for (int k = 0; k < R; ++k) x[k] = gld(p + (n0 + k * dn) * ts);
   } else {
-    const T* p = reinterpret_cast<const T*>(a.in) + vi.in_off;
-    const bool two = a.in_mode == IO_RP && (vi.flags & 1);
+    int src[R];
+    if (a.pre_map) {
 #pragma unroll
-    for (int k = 0; k < R; ++k) {
-      T re = (T)0, im = (T)0;
-      if (src[k] >= 0) {
-        re = gld(p + src[k] * ts);
-        if (two) im = gld(p + src[k] * ts + a.in_ld);
+      for (int k = 0; k < R; ++k) {
+        const int n = n0 + k * dn;
+        src[k] = n < Lin ? gld(a.pre_map + n) : -1;
       }
-      x[k] = cmake(re, im);
+    } else {
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        const int n = n0 + k * dn;
+        src[k] = n < Lin ? n : -1;
+      }
+    }
+    if (a.in_mode == IO_C) {
+      const C* p = reinterpret_cast<const C*>(a.in) + vi.in_off;
+#pragma unroll
+      for (int k = 0; k < R; ++k) x[k] = src[k] >= 0 ? gld(p + src[k] * ts) : zero;
+    } else {
+      const T* p = reinterpret_cast<const T*>(a.in) + vi.in_off;
+      const bool two = a.in_mode == IO_RP && (vi.flags & 1);
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        T re = (T)0, im = (T)0;
+        if (src[k] >= 0) {
+          re = gld(p + src[k] * ts);
+          if (two) im = gld(p + src[k] * ts + a.in_ld);
+        }
+        x[k] = cmake(re, im);
+      }
     }
   }
   if (a.pre_dc) {
@@ -133,6 +140,13 @@ __device__ __forceinline__ void fft_store_bfly(const FftArgs<T>& a, const VecInf
   if (a.scale != (T)1) {
 #pragma unroll
     for (int k = 0; k < R; ++k) x[k] = cscale(x[k], a.scale);
+  }
+  if (a.out_mode == IO_C && !a.post_map && !a.beta && n0 + (R - 1) * dn < Lout) {
+    // complex output, no row map, no accumulation, the whole butterfly inside the vector
+    C* p = reinterpret_cast<C*>(a.out) + vi.out_off;
+#pragma unroll
+    for (int k = 0; k < R; ++k) gst(p + (n0 + k * dn) * ts, x[k]);
+    return;
   }
   int dst[R];
   if (a.post_map) {
