@@ -21,6 +21,7 @@ import argparse
 import json
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -62,7 +63,8 @@ class Clocks:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # raw samples: FM_CLOCKS_DIR if set (to keep them), else the system temporary directory
+        self.path = os.path.join(os.environ.get("FM_CLOCKS_DIR", tempfile.gettempdir()), f"fm_clocks_rank{index}.csv")
 
     def __enter__(self):
         try:
