@@ -133,8 +133,12 @@ fm_status fm_out_dtype(fm_op A, fm_dtype in, fm_dtype* out);
 /* ---------------------------------------------------------------- transforms */
 
 /* Y = A X (forward, Eq. (3)) for ncols columns.  X: cols(A) x ncols block of type
- * xdt with leading dimension ldx; Y: rows(A) x ncols block of type ydt (must equal
- * fm_out_dtype(A, xdt)) with leading dimension ldy.  Y must not overlap X.
+ * xdt with leading dimension ldx; Y: rows(A) x ncols block of type ydt with leading
+ * dimension ldy.  ydt is fm_out_dtype(A, xdt), or, where that type is complex, the real
+ * type of the same precision (F32 for C64, F64 for C128): then Y = Re(A X).  The real
+ * part is what a real-valued parameterisation needs: for real x the map x -> A x into
+ * C^m, seen as R^2m, has the adjoint y -> Re(A^H y), so the gradient of a loss with
+ * respect to a real x is fm_backward with a real output type.  Y must not overlap X.
  * Intermediate buffers come from a per-operator workspace that grows on demand
  * (call fm_reserve first to keep the call free of allocation, e.g. before
  * capturing it in a CUDA graph). */
@@ -156,15 +160,18 @@ fm_status fm_reserve(fm_op A, int64_t ncols, fm_dtype xdt, void* stream);
  * computes the same result as fm_forward (adjoint = 0) or fm_backward (adjoint = 1) of
  * the Circulant operator C on ncols complex64 columns (X, Y: device buffers, leading
  * dimensions ldx, ldy >= n; Y must not overlap X), but the scratch of the two-pass plan
- * used for n > 16384 comes from a fixed 16 MiB array in the library's device image
- * (reserved on every GPU that loads the library, held until exit) instead of the
- * operator's growable workspace.  It calls no cudaMalloc, cudaFree or allocating routine.
+ * used for n > 16384 comes from a fixed 16 MiB array in the library's device image instead
+ * of the operator's growable workspace.  That array is reserved on a device when the first
+ * Circulant operator is built there (fm_circulant looks up its device address, which loads
+ * it) and held until the process exits.  The call itself calls no cudaMalloc, cudaFree or
+ * allocating routine and reads the address fm_circulant stored.
  * Limits and rules:
  *   - the scratch needed is n * ncols * 8 bytes when n > 16384 (nothing below that); a
- *     call needing more than 16 MiB returns FM_ERR_UNSUPPORTED: split the columns;
+ *     call needing more than 16 MiB returns FM_ERR_UNSUPPORTED: split the columns (n = 2^18
+ *     takes up to 8 columns per call);
  *   - C must come from fm_circulant on the current device (FM_ERR_INVALID_ARG otherwise);
- *   - the first call on a device looks up the array's device address (set-up); make that
- *     first call before capturing any stream;
+ *   - after cudaDeviceReset every operator of that device is invalid, and so is the stored
+ *     address: build a new Circulant operator there (which stores it again) before calling;
  *   - all calls share the one array, which keeps what the last call wrote (every element
  *     a call reads it has written first, so nothing needs clearing): calls that overlap
  *     on the GPU -- on different streams, or from different threads -- race, so serialise
@@ -223,11 +230,19 @@ typedef struct {
   int32_t accel;       /* 1 FISTA momentum, 0 ISTA                                    */
   int32_t mode;        /* 0: one persistent launch over the whole batch;
                           1: the same steps as separate per-instance launches       */
+  int32_t warm;        /* 0: cold start x_0 = y_1 = 0, t_1 = 1, lambda and L computed;
+                          1: resume a run that has taken k0 steps (fm_fista_batch only):
+                          x holds x_k0, y holds y_{k0+1}, rep->L and rep->lambda hold
+                          that run's L and lambda (read, not recomputed), and t_{k0+1}
+                          is rebuilt from t_1 = 1 by the same recurrence.  K1 steps, then
+                          K2 resumed steps, give the bits of K1 + K2 steps.           */
+  int32_t k0;          /* warm: steps the resumed run has taken (>= 0)                */
 } fm_fista_params;
 
 /* Per-instance results, DEVICE arrays of length `count` (any may be NULL):
  * L, lambda, final objective 1/2||A x - b||^2 + lambda ||x||_1, status (0 ok,
- * FM_ERR_NUMERIC if a non-finite value appeared). */
+ * FM_ERR_NUMERIC if a non-finite value appeared).  With p->warm = 1, L and lambda are
+ * also inputs (the values of the run being resumed). */
 typedef struct {
   double* L;
   double* lambda;
@@ -235,21 +250,35 @@ typedef struct {
   int32_t* status;
 } fm_fista_report;
 
-/* A batch of `count` instances, each A_i = Product(Partial(idx_i, n_i), Toeplitz(t_i))
- * with real t_i (n_i x n_i, n_i a power of two in [2^8, 2^14]) and m_i selected rows;
- * other operator shapes give FM_ERR_UNSUPPORTED.  Building the batch uploads a
- * work list (instances sorted by size) and allocates the per-instance state. */
+/* Batched FISTA on `batch` instances given as operators, each A_i =
+ * Product(Partial(idx_i, n_i), Toeplitz(t_i)) with real t_i (n_i x n_i, n_i a power of two in
+ * [2^8, 2^14]) and m_i selected rows (other shapes: FM_ERR_UNSUPPORTED).  b[i] (m_i floats) and
+ * x[i] (n_i floats, 8-byte aligned) are DEVICE pointers held in HOST arrays of `batch` entries.
+ * Every instance starts cold (p->warm must be 0).  The call builds the work list (instances
+ * sorted and grouped by size), uploads the pointer arrays, solves all instances in one
+ * launch (p->mode = 0) or one launch per instance (p->mode = 1), synchronises `stream` and
+ * frees what it built: it allocates, so it cannot be captured in a CUDA graph.  For
+ * repeated or captured solves, and to resume a run, build the batch once with
+ * fm_batch_create and call fm_fista_batch. */
+fm_status fm_fista(const fm_op* A, int64_t batch, const float* const* b, float* const* x, const fm_fista_params* p,
+                   const fm_fista_report* rep, void* stream);
+
+/* A batch of `count` instances of the form above, kept for repeated solves.  Building the
+ * batch uploads a work list (instances sorted by size) and allocates the per-instance
+ * state. */
 fm_status fm_batch_create(const fm_op* A, int64_t count, void* stream, fm_batch* out);
 void fm_batch_release(fm_batch B);
 /* Total rows (sum m_i) and columns (sum n_i) of the batch: the lengths of the packed
  * b and x buffers below. */
 fm_status fm_batch_sizes(fm_batch B, int64_t* total_rows, int64_t* total_cols);
 
-/* Solve every instance.  b: packed float32 measurements (instance i at offset
+/* Solve every instance of B.  b: packed float32 measurements (instance i at offset
  * sum_{j<i} m_j), x: packed float32 solutions (offset sum_{j<i} n_j, 8-byte aligned), both
- * device buffers.  No allocation and no host synchronisation: capturable in a CUDA graph. */
-fm_status fm_fista(fm_batch B, const float* b, float* x, const fm_fista_params* p,
-                   const fm_fista_report* rep, void* stream);
+ * device buffers.  y (optional, packed like x, 8-byte aligned; NULL = a buffer of the batch)
+ * receives the momentum state y_{K+1} so that the run can be resumed (p->warm = 1 reads it).
+ * No allocation and no host synchronisation: capturable in a CUDA graph. */
+fm_status fm_fista_batch(fm_batch B, const float* b, float* x, float* y, const fm_fista_params* p,
+                         const fm_fista_report* rep, void* stream);
 
 /* ---------------------------------------------------------------- misc */
 

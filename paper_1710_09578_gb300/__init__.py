@@ -21,7 +21,7 @@ from ._lib import (FM_HAD_BF16, FM_HAD_BF16X2, FM_HAD_FP32, FM_HAD_INT8, FmError
                    fm_fista_params, fm_fista_report)
 
 __all__ = ["Op", "fourier", "circulant", "toeplitz", "hadamard", "diag", "partial", "product",
-           "sum_", "blkdiag", "kron", "FmApply", "apply", "FistaBatch", "FmError",
+           "sum_", "blkdiag", "kron", "FmApply", "apply", "FistaBatch", "fista", "FmError",
            "FM_HAD_FP32", "FM_HAD_BF16", "FM_HAD_BF16X2", "FM_HAD_INT8", "launch_count"]
 
 _TORCH2FM = {torch.int8: _lib.FM_I8, torch.int32: _lib.FM_I32, torch.float32: _lib.FM_F32,
@@ -86,7 +86,8 @@ class Op:
     def out_dtype(self, dtype: torch.dtype) -> torch.dtype:
         return _FM2TORCH[_lib.fm_out_dtype(self._h, _TORCH2FM[dtype])]
 
-    def _apply(self, X: torch.Tensor, adjoint: bool, out: torch.Tensor | None = None) -> torch.Tensor:
+    def _apply(self, X: torch.Tensor, adjoint: bool, out: torch.Tensor | None = None,
+               real_out: bool = False) -> torch.Tensor:
         if not isinstance(X, torch.Tensor) or not X.is_cuda:
             raise TypeError("X must be a CUDA tensor")
         one = X.dim() == 1
@@ -100,6 +101,8 @@ class Op:
             raise ValueError(f"expected columns of length {nin}, got {X2.shape[1]}")
         k = X2.shape[0]
         odt = self.out_dtype(X2.dtype)
+        if real_out and odt.is_complex:
+            odt = torch.float32 if odt == torch.complex64 else torch.float64
         if out is None:
             Y = torch.empty((k, nout), dtype=odt, device=X2.device)
         else:
@@ -112,13 +115,13 @@ class Op:
         fn(self._h, X2.data_ptr(), ldx, _TORCH2FM[X2.dtype], Y.data_ptr(), ldy, _TORCH2FM[odt], k, _stream())
         return Y[0] if one and out is None else Y
 
-    def forward(self, X, out=None):
-        """phi_A(X) = A X (Eq. (3))."""
-        return self._apply(X, False, out)
+    def forward(self, X, out=None, real_out: bool = False):
+        """phi_A(X) = A X (Eq. (3)); real_out: Re(A X) when A X would be complex."""
+        return self._apply(X, False, out, real_out)
 
-    def backward(self, Y, out=None):
-        """beta_A(Y) = A^H Y (Eq. (4))."""
-        return self._apply(Y, True, out)
+    def backward(self, Y, out=None, real_out: bool = False):
+        """beta_A(Y) = A^H Y (Eq. (4)); real_out: Re(A^H Y), the adjoint of A on real inputs."""
+        return self._apply(Y, True, out, real_out)
 
     def reserve(self, ncols: int, dtype: torch.dtype):
         """Grow the workspace so that later calls on up to ncols columns allocate nothing."""
@@ -232,10 +235,8 @@ class FmApply(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, g):
-        gx = ctx.op.backward(g.contiguous())
-        if ctx.real_in and gx.is_complex():
-            gx = gx.real.contiguous()
-        return gx, None
+        # real x: the library returns Re(A^H g), the adjoint of x -> A x on real inputs
+        return ctx.op.backward(g.contiguous(), real_out=ctx.real_in), None
 
 
 def apply(op: Op, X: torch.Tensor) -> torch.Tensor:
@@ -261,20 +262,60 @@ class FistaBatch:
 
     def solve(self, b: torch.Tensor, x: torch.Tensor | None = None, iters: int = 200, power_iters: int = 20,
               lambda_rel: float = 0.01, safety: float = 1.05, accel: bool = True, mode: int = 0,
-              report: bool = False):
+              report: bool | dict = False, y: torch.Tensor | None = None, resume_from: int | None = None):
+        """Solve every instance (``fm_fista_batch``).
+
+        y (packed like x) receives the momentum state y_{K+1}.  ``resume_from=k0`` continues a
+        run that has taken k0 steps: x and y hold its x_k0 and y_{k0+1}, and ``report`` must be
+        the dict that run returned (its L and lambda are reused)."""
         if b.dtype != torch.float32 or not b.is_cuda or b.numel() != self.total_rows:
             raise ValueError("b must be a packed float32 CUDA tensor of the batch's total rows")
         if x is None:
+            if resume_from is not None:
+                raise ValueError("a resumed run needs its x")
             x = torch.empty(self.total_cols, dtype=torch.float32, device=b.device)
-        params = fm_fista_params(iters, power_iters, lambda_rel, safety, 1 if accel else 0, mode)
+        warm = resume_from is not None
+        if warm and (y is None or not isinstance(report, dict)):
+            raise ValueError("a resumed run needs its y and the report of the run it continues")
+        params = fm_fista_params(iters, power_iters, lambda_rel, safety, 1 if accel else 0, mode,
+                                 1 if warm else 0, int(resume_from or 0))
         rep = None
         out = None
         if report:
-            out = {"L": torch.empty(self.count, dtype=torch.float64, device=b.device),
-                   "lambda": torch.empty(self.count, dtype=torch.float64, device=b.device),
-                   "objective": torch.empty(self.count, dtype=torch.float64, device=b.device),
-                   "status": torch.empty(self.count, dtype=torch.int32, device=b.device)}
+            out = report if isinstance(report, dict) else {
+                "L": torch.empty(self.count, dtype=torch.float64, device=b.device),
+                "lambda": torch.empty(self.count, dtype=torch.float64, device=b.device),
+                "objective": torch.empty(self.count, dtype=torch.float64, device=b.device),
+                "status": torch.empty(self.count, dtype=torch.int32, device=b.device)}
             rep = fm_fista_report(out["L"].data_ptr(), out["lambda"].data_ptr(),
                                   out["objective"].data_ptr(), out["status"].data_ptr())
-        _lib.fm_fista(self._b, b.data_ptr(), x.data_ptr(), params, rep, _stream())
+        _lib.fm_fista_batch(self._b, b.data_ptr(), x.data_ptr(), None if y is None else y.data_ptr(),
+                            params, rep, _stream())
         return (x, out) if report else x
+
+
+def fista(ops, bs, xs=None, iters: int = 200, power_iters: int = 20, lambda_rel: float = 0.01,
+          safety: float = 1.05, accel: bool = True, mode: int = 0, report: bool = False):
+    """Solve independent instances given as separate tensors (``fm_fista``): ops[i] =
+    P_i T_i, bs[i] its float32 measurements, xs[i] (created if None) its solution."""
+    ops = list(ops)
+    if xs is None:
+        xs = [torch.empty(o.cols, dtype=torch.float32, device=b.device) for o, b in zip(ops, bs)]
+    for b, x, o in zip(bs, xs, ops):
+        if b.dtype != torch.float32 or x.dtype != torch.float32 or not b.is_cuda or not x.is_cuda:
+            raise ValueError("b and x must be float32 CUDA tensors")
+        if b.numel() != o.rows or x.numel() != o.cols or not b.is_contiguous() or not x.is_contiguous():
+            raise ValueError("b[i] must hold rows(A_i) and x[i] cols(A_i) contiguous floats")
+    params = fm_fista_params(iters, power_iters, lambda_rel, safety, 1 if accel else 0, mode, 0, 0)
+    rep, out = None, None
+    if report:
+        dev = bs[0].device
+        out = {"L": torch.empty(len(ops), dtype=torch.float64, device=dev),
+               "lambda": torch.empty(len(ops), dtype=torch.float64, device=dev),
+               "objective": torch.empty(len(ops), dtype=torch.float64, device=dev),
+               "status": torch.empty(len(ops), dtype=torch.int32, device=dev)}
+        rep = fm_fista_report(out["L"].data_ptr(), out["lambda"].data_ptr(),
+                              out["objective"].data_ptr(), out["status"].data_ptr())
+    _lib.fm_fista([o.handle for o in ops], [b.data_ptr() for b in bs], [x.data_ptr() for x in xs],
+                  params, rep, _stream())
+    return (xs, out) if report else xs

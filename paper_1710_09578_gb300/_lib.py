@@ -29,7 +29,8 @@ class FmError(RuntimeError):
 class fm_fista_params(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("power_iters", ctypes.c_int32),
                 ("lambda_rel", ctypes.c_double), ("safety", ctypes.c_double),
-                ("accel", ctypes.c_int32), ("mode", ctypes.c_int32)]
+                ("accel", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("warm", ctypes.c_int32), ("k0", ctypes.c_int32)]
 
 
 class fm_fista_report(ctypes.Structure):
@@ -73,7 +74,9 @@ _SIGS = {
     "fm_circulant_apply_noalloc": [_op, _i32, _p, _i64, _p, _i64, _i64, _p],
     "fm_batch_create": [_opp, _i64, _p, _opp],
     "fm_batch_sizes": [_p, ctypes.POINTER(_i64), ctypes.POINTER(_i64)],
-    "fm_fista": [_p, _p, _p, ctypes.POINTER(fm_fista_params), ctypes.POINTER(fm_fista_report), _p],
+    "fm_fista": [_opp, _i64, ctypes.POINTER(_p), ctypes.POINTER(_p), ctypes.POINTER(fm_fista_params),
+                 ctypes.POINTER(fm_fista_report), _p],
+    "fm_fista_batch": [_p, _p, _p, _p, ctypes.POINTER(fm_fista_params), ctypes.POINTER(fm_fista_report), _p],
     "fm_calibrate": [_op, _i64, _i32, _p, ctypes.POINTER(fm_tune_entry), _i32, ctypes.POINTER(_i32)],
     "fm_set_split": [_op, _i64, _i64, _p],
 }
@@ -220,10 +223,22 @@ def fm_batch_sizes(b):
     return r.value, c.value
 
 
-def fm_fista(b, b_ptr: int, x_ptr: int, params: fm_fista_params, report: fm_fista_report | None,
+def fm_fista(handles, b_ptrs, x_ptrs, params: fm_fista_params, report: fm_fista_report | None,
              stream: int = 0):
+    """Solve len(handles) instances; b_ptrs / x_ptrs: device pointers, one per instance."""
+    n = len(handles)
+    if len(b_ptrs) != n or len(x_ptrs) != n:
+        raise ValueError("one b and one x pointer per instance")
+    bp = (ctypes.c_void_p * n)(*b_ptrs)
+    xp = (ctypes.c_void_p * n)(*x_ptrs)
     rep = ctypes.byref(report) if report is not None else None
-    check(lib.fm_fista(b, b_ptr, x_ptr, ctypes.byref(params), rep, stream), "fm_fista")
+    check(lib.fm_fista(_arr(handles), n, bp, xp, ctypes.byref(params), rep, stream), "fm_fista")
+
+
+def fm_fista_batch(b, b_ptr: int, x_ptr: int, y_ptr: int | None, params: fm_fista_params,
+                   report: fm_fista_report | None, stream: int = 0):
+    rep = ctypes.byref(report) if report is not None else None
+    check(lib.fm_fista_batch(b, b_ptr, x_ptr, y_ptr, ctypes.byref(params), rep, stream), "fm_fista_batch")
 
 
 def fm_release(h):

@@ -203,8 +203,9 @@ static fm_status apply(fm_op A, bool adj, const void* X, int64_t ldx, fm_dtype x
   const int64_t nin = adj ? A->rows : A->cols, nout = adj ? A->cols : A->rows;
   fm_dtype nd;
   FM_TRY(natural_out_dtype(A, xdt, &nd));
-  if (nd != ydt) {
-    set_error("output dtype must be %d for this operator and input", (int)nd);
+  const bool real_part = is_complex(nd) && ydt == real_of(nd);
+  if (nd != ydt && !real_part) {
+    set_error("output dtype must be %d (or its real type) for this operator and input", (int)nd);
     return FM_ERR_DTYPE;
   }
   if (ncols == 0) return FM_OK;
@@ -293,6 +294,7 @@ fm_status fm_circulant(const void* c, int64_t n, fm_dtype dt, void* stream, fm_o
   if (s != FM_OK) return finish(A, s, out);
   DeviceTables* t;
   s = device_tables(A->device, &t);
+  if (s == FM_OK) s = noalloc_prepare(A->device);
   if (s == FM_OK) {
     if (n == 1) {
       A->L = 1;

@@ -51,14 +51,19 @@ struct FistaArgs {
   const FGroup* groups;
   int ngroups;
   int single_group;        // >= 0: only this group (one launch per instance)
-  const float* b;
-  float* x;
-  float* y;
+  const float* b;          // packed b (instance i at inst[i].b_off) ...
+  float* x;                // ... and packed x (at inst[i].x_off), or
+  const float* const* bp;  // per-instance pointers (device arrays of `count` entries)
+  float* const* xp;
+  float* y;                // FISTA momentum state y_{k+1}, packed like x
+  float* pw;               // power-iteration iterate, packed like x (may equal y)
   const float2* tw;        // W_{2^14}^m, FFT passes
   const float2* tw2;       // W_{2^15}^m, real-FFT pre/post steps
   int iters, power_iters;
   double lambda_rel, safety;
   int accel;
+  int warm;                // 1: resume from x_k, y_{k+1} with L, lambda read from rep_L, rep_lambda
+  int k0;                  // warm: steps already taken
   double* rep_L;
   double* rep_lambda;
   double* rep_obj;
@@ -73,7 +78,10 @@ struct VState {
   const float2* spec;
   const int32_t* idx;
   const int32_t* inv;
-  int64_t b_off, x_off;
+  const float* b;       // this instance's measurements
+  float* x;             // its solution x_k
+  float* y;             // its momentum state y_{k+1}
+  float* pw;            // its power-iteration iterate
   int m, valid, inst, pad;
   float invL, thr;
   double cap, lam, L, acc;
@@ -106,15 +114,24 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Add val into vs[v].acc; one atomic per warp when the whole warp works on the same vector.
-__device__ __forceinline__ void vec_add(VState* vs, int v, double val) {
-  const int v0 = __shfl_sync(0xffffffffu, v, 0);
-  if (__all_sync(0xffffffffu, v == v0)) {
-    val = warp_sum(val);
-    if ((threadIdx.x & 31) == 0) atomicAdd(&vs[v0].acc, val);
-  } else {
-    atomicAdd(&vs[v].acc, val);
+// Sums over the elements of each vector, in a fixed order (runs are bit-reproducible).  The
+// element loops of a tile visit q = threadIdx.x + i * kFThreads over V * Nc = 2^14 elements, so
+// the 32 lanes of a warp always hold 32 consecutive elements of one vector (Nc >= 256):
+// vec_part stores the warp's sum at slot q / 32, vec_finish adds a vector's slots in order.
+__device__ __forceinline__ void vec_part(double* part, int q, double val) {
+  val = warp_sum(val);
+  if ((threadIdx.x & 31) == 0) part[q >> 5] = val;
+}
+template <int LOGL>
+__device__ __forceinline__ void vec_finish(VState* vs, const double* part) {
+  constexpr int V = FGeo<LOGL>::V, W = (1 << LOGL) >> 5;
+  __syncthreads();
+  for (int v = threadIdx.x; v < V; v += kFThreads) {
+    double acc = 0.0;
+    for (int w = 0; w < W; ++w) acc += part[v * W + w];
+    vs[v].acc = acc;
   }
+  __syncthreads();
 }
 
 __device__ __forceinline__ void vec_max(VState* vs, int v, float val) {
@@ -140,7 +157,7 @@ __device__ __forceinline__ void tile_fft(float2* s, int dir, const float2* tw) {
 // tile_fft(-1) whose first pass reads the residual u = P^T (P T y - b) instead of T y
 // (the MODE_RESID row mask of mask_rows applied to each element as it is read).
 template <int LOGL>
-__device__ __forceinline__ void tile_fft_resid(float2* s, const VState* vs, const float* b, const float2* tw) {
+__device__ __forceinline__ void tile_fft_resid(float2* s, const VState* vs, const float2* tw) {
   constexpr int LOGV = FGeo<LOGL>::LOGV, Nc = 1 << LOGL;
   constexpr bool VF = FGeo<LOGL>::VF;
   using S = Sched<LOGL, ept_lmax<kFEpt>()>;
@@ -153,7 +170,7 @@ __device__ __forceinline__ void tile_fft_resid(float2* s, const VState* vs, cons
     bfly2<VF, kFThreads, LOGL, LOGV, LR0>(q, j, v);
     const bool valid = vs[v].valid;
     const int32_t* inv = vs[v].inv;
-    const float* bb = b + vs[v].b_off;
+    const float* bb = vs[v].b;
 #pragma unroll
     for (int k = 0; k < R; ++k) {
       const int kk = j + k * M;
@@ -178,8 +195,7 @@ __device__ __forceinline__ void tile_fft_resid(float2* s, const VState* vs, cons
 // y_{k+1} = x_k + beta (x_k - x_{k-1}) go to x and y, and pack(y_{k+1}) is what the pass
 // writes back to the tile for the next step.
 template <int LOGL>
-__device__ __forceinline__ void tile_ifft_update(float2* s, const VState* vs, float* x, float* y, float beta,
-                                                 const float2* tw) {
+__device__ __forceinline__ void tile_ifft_update(float2* s, const VState* vs, float beta, const float2* tw) {
   constexpr int LOGV = FGeo<LOGL>::LOGV, Nc = 1 << LOGL;
   constexpr bool VF = FGeo<LOGL>::VF;
   using S = Sched<LOGL, ept_lmax<kFEpt>()>;
@@ -192,7 +208,8 @@ __device__ __forceinline__ void tile_ifft_update(float2* s, const VState* vs, fl
     int j, v;
     bfly2<VF, kFThreads, LOGL, LOGV, LRL>(q, j, v);
     const bool valid = vs[v].valid;
-    const int64_t xo = vs[v].x_off;
+    float* x = vs[v].x;
+    float* y = vs[v].y;
     const float invL = vs[v].invL, thr = vs[v].thr;
 #pragma unroll
     for (int k = 0; k < R; ++k) {
@@ -200,7 +217,7 @@ __device__ __forceinline__ void tile_ifft_update(float2* s, const VState* vs, fl
       float2 ny = make_float2(0.f, 0.f);
       if (valid && kk < (Nc >> 1)) {
         const float2 g = r[q * R + k];
-        const int64_t o = xo + 2 * kk;
+        const int o = 2 * kk;
         const float2 yv = ld_state(y + o);
         const float2 xv = ld_state(x + o);
         const float z0 = yv.x - g.x * invL, z1 = yv.y - g.y * invL;
@@ -265,14 +282,14 @@ __device__ __forceinline__ float unpack(const float2* s, int m, int v) {
   return (m & 1) ? z.y : z.x;
 }
 
-// Z <- pack([w; 0]) where w is the length-n real vector at src + x_off of each vector
+// Z <- pack([w; 0]) where w is the length-n real vector (vs[v].*src) of each vector
 template <int LOGL>
-__device__ void pack_from(float2* s, VState* vs, const float* src) {
+__device__ void pack_from(float2* s, VState* vs, float* VState::*src) {
   constexpr int Nc = 1 << LOGL, V = FGeo<LOGL>::V;
   for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
     const int v = q >> LOGL, k = q & (Nc - 1);
     float2 z = make_float2(0.f, 0.f);
-    if (vs[v].valid && k < (Nc >> 1)) z = ld_state(src + vs[v].x_off + 2 * k);
+    if (vs[v].valid && k < (Nc >> 1)) z = ld_state(vs[v].*src + 2 * k);
     *zaddr<LOGL>(s, k, v) = z;
   }
 }
@@ -293,7 +310,7 @@ __device__ void apply_T(float2* s, VState* vs, int adjoint, const float2* tw, co
 // the selected entries are added into vs[v].acc.
 enum { MODE_MASK = 0, MODE_RESID = 1, MODE_B = 2 };
 template <int LOGL, int MODE>
-__device__ void mask_rows(float2* s, VState* vs, const float* b, bool sumsq) {
+__device__ void mask_rows(float2* s, VState* vs, double* part, bool sumsq) {
   constexpr int Nc = 1 << LOGL, V = FGeo<LOGL>::V;
   for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
     const int v = q >> LOGL, k = q & (Nc - 1);
@@ -303,19 +320,24 @@ __device__ void mask_rows(float2* s, VState* vs, const float* b, bool sumsq) {
     if (vs[v].valid && k < (Nc >> 1)) {
       const float2 z = MODE == MODE_B ? make_float2(0.f, 0.f) : *p;
       const int2 r = *reinterpret_cast<const int2*>(vs[v].inv + 2 * k);
-      const float* bb = b + vs[v].b_off;
+      const float* bb = vs[v].b;
       if (r.x >= 0) u.x = MODE == MODE_B ? bb[r.x] : (MODE == MODE_RESID ? z.x - bb[r.x] : z.x);
       if (r.y >= 0) u.y = MODE == MODE_B ? bb[r.y] : (MODE == MODE_RESID ? z.y - bb[r.y] : z.y);
       ss = (double)u.x * (double)u.x + (double)u.y * (double)u.y;
     }
     *p = u;
-    if (sumsq) vec_add(vs, v, ss);
+    if (sumsq) vec_part(part, q, ss);
   }
 }
 
-// Every step of one group: lambda, L, K FISTA steps and the objective.
+// t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2, one compiled copy for every caller, so that a run
+// resumed after k0 steps rebuilds exactly the t a continuous run would hold.
+__device__ __noinline__ double fista_t_next(double t) { return 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t)); }
+
+// Every step of one group: lambda, L, K FISTA steps and the objective.  A warm start skips
+// lambda and L (read back from the report of the run it resumes) and the zero start.
 template <int LOGL>
-__device__ void fista_group(const FistaArgs& a, const FGroup& G, float2* s, VState* vs, double* s_t) {
+__device__ void fista_group(const FistaArgs& a, const FGroup& G, float2* s, VState* vs, double* part, double* s_t) {
   constexpr int Nc = 1 << LOGL, V = FGeo<LOGL>::V;
   for (int v = threadIdx.x; v < V; v += kFThreads) {
     VState w = {};
@@ -326,112 +348,129 @@ __device__ void fista_group(const FistaArgs& a, const FGroup& G, float2* s, VSta
       w.spec = in.spec;
       w.idx = in.idx;
       w.inv = in.inv;
-      w.b_off = in.b_off;
-      w.x_off = in.x_off;
+      w.b = a.bp ? a.bp[ii] : a.b + in.b_off;
+      w.x = a.xp ? a.xp[ii] : a.x + in.x_off;
+      w.y = a.y + in.x_off;
+      w.pw = a.pw + in.x_off;
       w.m = in.m;
       w.cap = in.cap;
       w.inst = ii;
+      if (a.warm) {
+        w.lam = a.rep_lambda[ii];
+        w.L = a.rep_L[ii];
+      }
     }
     vs[v] = w;
   }
   __syncthreads();
 
-  // ---- lambda = lambda_rel * ||A^T b||_inf
-  mask_rows<LOGL, MODE_B>(s, vs, a.b, false);
-  apply_T<LOGL>(s, vs, 1, a.tw, a.tw2);
-  for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
-    const int v = q >> LOGL;
-    if (vs[v].valid) vec_max(vs, v, unpack<LOGL>(s, q & (Nc - 1), v));
-  }
-  __syncthreads();
-  for (int v = threadIdx.x; v < V; v += kFThreads) vs[v].lam = a.lambda_rel * (double)__uint_as_float(vs[v].amax);
-
-  // ---- power iteration on A^T A from ones / sqrt(n), the iterate kept in y
-  {
-    const float v0 = rsqrtf((float)Nc);
-    for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
-      const int v = q >> LOGL;
-      if (vs[v].valid) __stcg(a.y + vs[v].x_off + (q & (Nc - 1)), v0);
-    }
-  }
-  for (int it = 0; it < a.power_iters; ++it) {
-    __syncthreads();
-    pack_from<LOGL>(s, vs, a.y);
-    apply_T<LOGL>(s, vs, 0, a.tw, a.tw2);
-    mask_rows<LOGL, MODE_MASK>(s, vs, a.b, false);
+  if (!a.warm) {
+    // ---- lambda = lambda_rel * ||A^T b||_inf
+    mask_rows<LOGL, MODE_B>(s, vs, part, false);
     apply_T<LOGL>(s, vs, 1, a.tw, a.tw2);
-    for (int v = threadIdx.x; v < V; v += kFThreads) vs[v].acc = 0.0;
-    __syncthreads();
     for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
       const int v = q >> LOGL;
-      const float w = unpack<LOGL>(s, q & (Nc - 1), v);
-      vec_add(vs, v, (double)w * (double)w);
+      if (vs[v].valid) vec_max(vs, v, unpack<LOGL>(s, q & (Nc - 1), v));
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
-      const int v = q >> LOGL;
-      if (vs[v].valid) {
-        const double nrm = sqrt(vs[v].acc);
-        const float w = unpack<LOGL>(s, q & (Nc - 1), v);
-        __stcg(a.y + vs[v].x_off + (q & (Nc - 1)), nrm > 0.0 ? (float)((double)w / nrm) : 0.f);
+    for (int v = threadIdx.x; v < V; v += kFThreads) vs[v].lam = a.lambda_rel * (double)__uint_as_float(vs[v].amax);
+
+    // ---- power iteration on A^T A from ones / sqrt(n), the iterate kept in pw
+    {
+      const float v0 = rsqrtf((float)Nc);
+      for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
+        const int v = q >> LOGL;
+        if (vs[v].valid) __stcg(vs[v].pw + (q & (Nc - 1)), v0);
       }
     }
+    for (int it = 0; it < a.power_iters; ++it) {
+      __syncthreads();
+      pack_from<LOGL>(s, vs, &VState::pw);
+      apply_T<LOGL>(s, vs, 0, a.tw, a.tw2);
+      mask_rows<LOGL, MODE_MASK>(s, vs, part, false);
+      apply_T<LOGL>(s, vs, 1, a.tw, a.tw2);
+      __syncthreads();
+      for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
+        const int v = q >> LOGL;
+        const float w = unpack<LOGL>(s, q & (Nc - 1), v);
+        vec_part(part, q, (double)w * (double)w);
+      }
+      vec_finish<LOGL>(vs, part);
+      for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
+        const int v = q >> LOGL;
+        if (vs[v].valid) {
+          const double nrm = sqrt(vs[v].acc);
+          const float w = unpack<LOGL>(s, q & (Nc - 1), v);
+          __stcg(vs[v].pw + (q & (Nc - 1)), nrm > 0.0 ? (float)((double)w / nrm) : 0.f);
+        }
+      }
+    }
+    // lam_hat = ||A v||^2, L = min(safety * lam_hat, cap)
+    __syncthreads();
+    pack_from<LOGL>(s, vs, &VState::pw);
+    apply_T<LOGL>(s, vs, 0, a.tw, a.tw2);
+    mask_rows<LOGL, MODE_MASK>(s, vs, part, true);
+    vec_finish<LOGL>(vs, part);
+    for (int v = threadIdx.x; v < V; v += kFThreads) {
+      double L = a.safety * vs[v].acc;
+      if (vs[v].cap < L) L = vs[v].cap;
+      vs[v].L = L;
+    }
   }
-  // lam_hat = ||A v||^2, L = min(safety * lam_hat, cap)
-  __syncthreads();
-  for (int v = threadIdx.x; v < V; v += kFThreads) vs[v].acc = 0.0;
-  pack_from<LOGL>(s, vs, a.y);
-  apply_T<LOGL>(s, vs, 0, a.tw, a.tw2);
-  mask_rows<LOGL, MODE_MASK>(s, vs, a.b, true);
-  __syncthreads();
   for (int v = threadIdx.x; v < V; v += kFThreads) {
-    double L = a.safety * vs[v].acc;
-    if (vs[v].cap < L) L = vs[v].cap;
-    vs[v].L = L;
+    const double L = vs[v].L;
     vs[v].invL = L > 0.0 ? (float)(1.0 / L) : 0.f;
     vs[v].thr = L > 0.0 ? (float)(vs[v].lam / L) : 0.f;
   }
-  // ---- FISTA from x_0 = y_1 = 0, t_1 = 1; the tile holds pack(y_k) at the top of a step
-  for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
-    const int v = q >> LOGL;
-    if (vs[v].valid) {
-      __stcg(a.x + vs[v].x_off + (q & (Nc - 1)), 0.f);
-      __stcg(a.y + vs[v].x_off + (q & (Nc - 1)), 0.f);
+  // ---- FISTA; the tile holds pack(y_k) at the top of a step.  Cold: x_0 = y_1 = 0, t_1 = 1.
+  //      Warm: x and y hold x_k0 and y_{k0+1}; t_{k0+1} follows from t_1 = 1 by the recurrence.
+  if (a.warm) {
+    __syncthreads();
+    pack_from<LOGL>(s, vs, &VState::y);
+    if (threadIdx.x == 0) {
+      double t = 1.0;
+      if (a.accel)
+        for (int k = 0; k < a.k0; ++k) t = fista_t_next(t);
+      *s_t = t;
     }
-    *zaddr<LOGL>(s, q & (Nc - 1), v) = make_float2(0.f, 0.f);
+  } else {
+    for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
+      const int v = q >> LOGL;
+      if (vs[v].valid) {
+        __stcg(vs[v].x + (q & (Nc - 1)), 0.f);
+        __stcg(vs[v].y + (q & (Nc - 1)), 0.f);
+      }
+      *zaddr<LOGL>(s, q & (Nc - 1), v) = make_float2(0.f, 0.f);
+    }
+    if (threadIdx.x == 0) *s_t = 1.0;
   }
-  if (threadIdx.x == 0) *s_t = 1.0;
   for (int k = 0; k < a.iters; ++k) {
     __syncthreads();
     const double t = *s_t;
-    const double tn = a.accel ? 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t)) : 1.0;
+    const double tn = a.accel ? fista_t_next(t) : 1.0;
     const float beta = a.accel ? (float)((t - 1.0) / tn) : 0.f;
     // A y_k, the residual (fused into the first pass of the next transform), A^T of it,
     // and the step (fused into the last pass of the inverse transform)
     apply_T<LOGL>(s, vs, 0, a.tw, a.tw2);
-    tile_fft_resid<LOGL>(s, vs, a.b, a.tw);
+    tile_fft_resid<LOGL>(s, vs, a.tw);
     tile_spectral<LOGL>(s, vs, 1, a.tw2);
     __syncthreads();
-    tile_ifft_update<LOGL>(s, vs, a.x, a.y, beta, a.tw);
+    tile_ifft_update<LOGL>(s, vs, beta, a.tw);
     if (threadIdx.x == 0) *s_t = tn;
   }
   // ---- objective 1/2 ||A x - b||^2 + lambda ||x||_1 and status
   __syncthreads();
-  for (int v = threadIdx.x; v < V; v += kFThreads) vs[v].acc = 0.0;
-  pack_from<LOGL>(s, vs, a.x);
+  pack_from<LOGL>(s, vs, &VState::x);
   apply_T<LOGL>(s, vs, 0, a.tw, a.tw2);
-  mask_rows<LOGL, MODE_RESID>(s, vs, a.b, true);
-  __syncthreads();
+  mask_rows<LOGL, MODE_RESID>(s, vs, part, true);
+  vec_finish<LOGL>(vs, part);
   for (int v = threadIdx.x; v < V; v += kFThreads) vs[v].cap = 0.5 * vs[v].acc;  // reuse cap: data term
-  __syncthreads();
-  for (int v = threadIdx.x; v < V; v += kFThreads) vs[v].acc = 0.0;
-  __syncthreads();
   for (int q = threadIdx.x; q < V * Nc; q += kFThreads) {
     const int v = q >> LOGL;
-    const float xv = vs[v].valid ? __ldcg(a.x + vs[v].x_off + (q & (Nc - 1))) : 0.f;
-    vec_add(vs, v, fabs((double)xv));
+    const float xv = vs[v].valid ? __ldcg(vs[v].x + (q & (Nc - 1))) : 0.f;
+    vec_part(part, q, fabs((double)xv));
   }
-  __syncthreads();
+  vec_finish<LOGL>(vs, part);
   for (int v = threadIdx.x; v < V; v += kFThreads) {
     if (!vs[v].valid) continue;
     const int ii = vs[v].inst;
@@ -449,6 +488,7 @@ __global__ void __launch_bounds__(kFThreads, 1) fista_kernel(const __grid_consta
   VState* vs = reinterpret_cast<VState*>(smem_raw + fft_vinfo_offset<float2>(kFE));
   __shared__ int s_group;
   __shared__ double s_t;
+  __shared__ double s_part[kFE / 32];   // per-warp partial sums (vec_part)
   bool first = true;
   while (true) {
     __syncthreads();
@@ -462,13 +502,13 @@ __global__ void __launch_bounds__(kFThreads, 1) fista_kernel(const __grid_consta
     if (gi < 0 || gi >= a.ngroups) break;
     const FGroup G = a.groups[gi];
     switch (G.logn) {
-      case 8: fista_group<8>(a, G, s, vs, &s_t); break;
-      case 9: fista_group<9>(a, G, s, vs, &s_t); break;
-      case 10: fista_group<10>(a, G, s, vs, &s_t); break;
-      case 11: fista_group<11>(a, G, s, vs, &s_t); break;
-      case 12: fista_group<12>(a, G, s, vs, &s_t); break;
-      case 13: fista_group<13>(a, G, s, vs, &s_t); break;
-      default: fista_group<14>(a, G, s, vs, &s_t); break;
+      case 8: fista_group<8>(a, G, s, vs, s_part, &s_t); break;
+      case 9: fista_group<9>(a, G, s, vs, s_part, &s_t); break;
+      case 10: fista_group<10>(a, G, s, vs, s_part, &s_t); break;
+      case 11: fista_group<11>(a, G, s, vs, s_part, &s_t); break;
+      case 12: fista_group<12>(a, G, s, vs, s_part, &s_t); break;
+      case 13: fista_group<13>(a, G, s, vs, s_part, &s_t); break;
+      default: fista_group<14>(a, G, s, vs, s_part, &s_t); break;
     }
   }
 }
@@ -621,28 +661,37 @@ fm_status fm_batch_sizes(fm_batch B, int64_t* rows, int64_t* cols) {
   return FM_OK;
 }
 
-fm_status fm_fista(fm_batch B, const float* b, float* x, const fm_fista_params* p, const fm_fista_report* rep,
-                   void* stream) {
-  clear_error();
-  if (!B || !b || !x || !p) { set_error("null pointer"); return FM_ERR_INVALID_ARG; }
-  if ((uintptr_t)x % 8) { set_error("x must be 8-byte aligned"); return FM_ERR_INVALID_ARG; }
+static fm_status check_params(const fm_fista_params* p, const fm_fista_report* rep) {
   if (p->iters < 0 || p->power_iters < 1 || !(p->safety > 0.0) || !(p->lambda_rel >= 0.0) ||
-      (p->mode != 0 && p->mode != 1)) {
+      (p->mode != 0 && p->mode != 1) || (p->warm != 0 && p->warm != 1) || p->k0 < 0) {
     set_error("bad FISTA parameters");
     return FM_ERR_INVALID_ARG;
   }
+  if (p->warm && (!rep || !rep->L || !rep->lambda)) {
+    set_error("a warm start reads L and lambda of the run it resumes from rep->L and rep->lambda");
+    return FM_ERR_INVALID_ARG;
+  }
+  return FM_OK;
+}
+
+// Launch the solve of every instance of B (bp, xp: per-instance pointer arrays on the device,
+// or NULL for the packed b and x).
+static fm_status fista_run(fm_batch B, const float* b, float* x, const float* const* bp, float* const* xp,
+                           float* y, const fm_fista_params* p, const fm_fista_report* rep, cudaStream_t st) {
   int dev = 0;
   FM_CUDA(cudaGetDevice(&dev));
   if (dev != B->device) { set_error("batch lives on device %d, current is %d", B->device, dev); return FM_ERR_INVALID_ARG; }
   DeviceTables* tabs = device_tables_if_ready(dev);
   if (!tabs) { set_error("device tables missing"); return FM_ERR_INVALID_ARG; }
-  cudaStream_t st = (cudaStream_t)stream;
   FistaArgs a;
   a.inst = B->inst;
   a.order = B->order;
   a.b = b;
   a.x = x;
-  a.y = B->y;
+  a.bp = bp;
+  a.xp = xp;
+  a.y = y ? y : B->y;
+  a.pw = B->y;
   a.tw = tabs->tw32;
   a.tw2 = B->tw2;
   a.iters = p->iters;
@@ -650,6 +699,8 @@ fm_status fm_fista(fm_batch B, const float* b, float* x, const fm_fista_params* 
   a.lambda_rel = p->lambda_rel;
   a.safety = p->safety;
   a.accel = p->accel ? 1 : 0;
+  a.warm = p->warm;
+  a.k0 = p->k0;
   a.rep_L = rep ? rep->L : nullptr;
   a.rep_lambda = rep ? rep->lambda : nullptr;
   a.rep_obj = rep ? rep->objective : nullptr;
@@ -674,6 +725,52 @@ fm_status fm_fista(fm_batch B, const float* b, float* x, const fm_fista_params* 
     FM_TRY(after_launch("fista_kernel"));
   }
   return FM_OK;
+}
+
+fm_status fm_fista_batch(fm_batch B, const float* b, float* x, float* y, const fm_fista_params* p,
+                         const fm_fista_report* rep, void* stream) {
+  clear_error();
+  if (!B || !b || !x || !p) { set_error("null pointer"); return FM_ERR_INVALID_ARG; }
+  if ((uintptr_t)x % 8 || (uintptr_t)y % 8) { set_error("x and y must be 8-byte aligned"); return FM_ERR_INVALID_ARG; }
+  FM_TRY(check_params(p, rep));
+  if (p->warm && !y) { set_error("a warm start needs the momentum state y of the run it resumes"); return FM_ERR_INVALID_ARG; }
+  return fista_run(B, b, x, nullptr, nullptr, y, p, rep, (cudaStream_t)stream);
+}
+
+fm_status fm_fista(const fm_op* A, int64_t batch, const float* const* b, float* const* x, const fm_fista_params* p,
+                   const fm_fista_report* rep, void* stream) {
+  clear_error();
+  if (!A || !b || !x || !p || batch < 1) { set_error("null pointer or empty batch"); return FM_ERR_INVALID_ARG; }
+  FM_TRY(check_params(p, rep));
+  if (p->warm) { set_error("fm_fista starts cold; resume a run through fm_fista_batch"); return FM_ERR_UNSUPPORTED; }
+  for (int64_t i = 0; i < batch; ++i) {
+    if (!b[i] || !x[i]) { set_error("instance %lld: null b or x", (long long)i); return FM_ERR_INVALID_ARG; }
+    if ((uintptr_t)x[i] % 8) { set_error("instance %lld: x must be 8-byte aligned", (long long)i); return FM_ERR_INVALID_ARG; }
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  fm_batch B = nullptr;
+  FM_TRY(fm_batch_create(A, batch, stream, &B));
+  void* ptrs = nullptr;
+  cudaError_t e = cudaMalloc(&ptrs, 2 * sizeof(void*) * (size_t)batch);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ptrs, b, sizeof(void*) * batch, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync((void**)ptrs + batch, x, sizeof(void*) * batch, cudaMemcpyHostToDevice, st);
+  fm_status s = FM_OK;
+  if (e != cudaSuccess) {
+    set_error("fm_fista: pointer upload: %s", cudaGetErrorString(e));
+    s = e == cudaErrorMemoryAllocation ? FM_ERR_OOM : FM_ERR_CUDA;
+  }
+  if (s == FM_OK)
+    s = fista_run(B, nullptr, nullptr, (const float* const*)ptrs, (float* const*)((void**)ptrs + batch), nullptr,
+                  p, rep, st);
+  e = cudaStreamSynchronize(st);
+  if (s == FM_OK && e != cudaSuccess) {
+    set_error("fm_fista: %s", cudaGetErrorString(e));
+    s = FM_ERR_CUDA;
+  }
+  if (ptrs) cudaFree(ptrs);
+  fm_batch_release(B);
+  return s;
 }
 
 }  // extern "C"

@@ -92,6 +92,11 @@ inline int dtype_size(fm_dtype d) {
   }
   return 0;
 }
+inline fm_dtype real_of(fm_dtype d) {
+  if (d == FM_C64) return FM_F32;
+  if (d == FM_C128) return FM_F64;
+  return d;
+}
 inline fm_dtype complex_of(fm_dtype d) {
   if (d == FM_F32) return FM_C64;
   if (d == FM_F64) return FM_C128;
@@ -110,6 +115,10 @@ struct DeviceTables {
 fm_status device_tables(int device, DeviceTables** out);
 // The tables of `device` if they exist already, else nullptr (never allocates).
 DeviceTables* device_tables_if_ready(int device);
+
+// Look up (and so reserve) the static scratch of fm_circulant_apply_noalloc on `device`, the
+// current device; called when a Circulant operator is built there (noalloc.cu).
+fm_status noalloc_prepare(int device);
 
 // ------------------------------------------------------------------ operators
 enum OpKind {

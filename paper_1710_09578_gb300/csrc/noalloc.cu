@@ -7,9 +7,9 @@
 // per-operator workspace on demand, which such callers cannot allow.  This entry point
 // applies a Circulant operator to complex64 columns with the scratch of the two-pass
 // plan (long transforms, n > 16384) taken from a fixed array that lives in the library's
-// device image instead: it is reserved when the library is loaded on a GPU and held
-// until the process exits.  The operator itself is built beforehand with fm_circulant,
-// which does allocate.
+// device image instead: it is reserved on a device when the first Circulant operator is
+// built there and held until the process exits.  The operator itself is built beforehand
+// with fm_circulant, which does allocate.
 #include <mutex>
 
 #include "exec.h"
@@ -20,24 +20,30 @@ namespace fm {
 constexpr size_t kNoallocScratchBytes = (size_t)16 << 20;
 static __device__ __align__(256) float2 g_noalloc_scratch[kNoallocScratchBytes / sizeof(float2)];
 
-// Device address of g_noalloc_scratch, looked up once per device with that device current.
+// Device address of g_noalloc_scratch per device.  The library's device code is loaded
+// lazily, so looking the address up is what loads this array's module and reserves its
+// 16 MiB on the device: fm_circulant does it (construction allocates anyway), and the
+// entry point below only reads the cached value.
 static std::mutex g_noalloc_mu;
 static void* g_noalloc_ptr[64] = {nullptr};
 
-static fm_status noalloc_scratch(int dev, void** out) {
+fm_status noalloc_prepare(int dev) {
   if (dev < 0 || dev >= 64) { set_error("device %d out of range", dev); return FM_ERR_INVALID_ARG; }
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      set_error("cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
-      return FM_ERR_CUDA;
-    }
-    g_noalloc_ptr[dev] = p;
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    set_error("cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? FM_ERR_OOM : FM_ERR_CUDA;
   }
-  *out = g_noalloc_ptr[dev];
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  g_noalloc_ptr[dev] = p;
   return FM_OK;
+}
+
+static void* noalloc_scratch(int dev) {
+  if (dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  return g_noalloc_ptr[dev];
 }
 
 }  // namespace fm
@@ -83,8 +89,8 @@ extern "C" fm_status fm_circulant_apply_noalloc(fm_op C, int adjoint, const void
               ctx.peak, kNoallocScratchBytes);
     return FM_ERR_UNSUPPORTED;
   }
-  void* scratch = nullptr;
-  FM_TRY(noalloc_scratch(dev, &scratch));
+  void* scratch = noalloc_scratch(dev);
+  if (!scratch) { set_error("the static scratch of device %d is not set up: build the operator there", dev); return FM_ERR_INVALID_ARG; }
   ctx.dry = false;
   ctx.base = (char*)scratch;
   ctx.cap = kNoallocScratchBytes;

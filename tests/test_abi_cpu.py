@@ -29,6 +29,49 @@ def test_every_declared_symbol_is_exported(L):
     assert sorted(names) == sorted(L.EXPORTED)
 
 
+def _signature(name):
+    src = open(os.path.join(ROOT, "include", "fm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    m = re.search(r"fm_status\s+" + name + r"\s*\(([^;]*)\);", src)
+    assert m, name
+    return [" ".join(a.split()) for a in m.group(1).split(",")]
+
+
+def test_fista_signature_is_the_operator_batch_form():
+    # fm_fista takes the batch as operators plus one b and one x buffer per instance
+    # (A, batch, b[], x[], params, report, stream)
+    assert _signature("fm_fista") == [
+        "const fm_op* A", "int64_t batch", "const float* const* b", "float* const* x",
+        "const fm_fista_params* p", "const fm_fista_report* rep", "void* stream"]
+    assert _signature("fm_fista_batch")[:5] == [
+        "fm_batch B", "const float* b", "float* x", "float* y", "const fm_fista_params* p"]
+
+
+def test_fista_params_layout(L):
+    import ctypes
+    assert ctypes.sizeof(L.fm_fista_params) == 40
+    assert L.fm_fista_params.warm.offset == 32 and L.fm_fista_params.k0.offset == 36
+
+
+def test_fista_host_validation(L):
+    p = L.fm_fista_params(10, 20, 0.01, 1.05, 1, 0, 0, 0)
+    with pytest.raises(L.FmError) as e:
+        L.fm_fista([], [], [], p, None)                     # empty batch
+    assert e.value.status == 1
+    bad = L.fm_fista_params(-1, 20, 0.01, 1.05, 1, 0, 0, 0)
+    with pytest.raises(L.FmError) as e:
+        L.fm_fista([1], [8], [16], bad, None)              # negative step count
+    assert e.value.status == 1
+    warm = L.fm_fista_params(10, 20, 0.01, 1.05, 1, 0, 1, 5)
+    rep = L.fm_fista_report(8, 8, 0, 0)
+    with pytest.raises(L.FmError) as e:
+        L.fm_fista([1], [8], [16], warm, rep)              # a resume goes through the batch form
+    assert e.value.status == 4
+    with pytest.raises(L.FmError) as e:
+        L.fm_fista([1], [8], [0], p, None)                 # null x
+    assert e.value.status == 1
+
+
 def test_status_strings_and_version(L):
     for s in range(10):
         assert L.fm_status_string(s) and L.fm_status_string(s) != "unknown status"

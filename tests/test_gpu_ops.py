@@ -523,6 +523,106 @@ def test_autograd_hadamard_real(fm):
         assert abs(fd - x.grad[0, j].item()) <= 1e-3 * max(1.0, abs(fd))
 
 
+def _fd_check(fm, A, X, g, grad, v, eps=0.5, tol=1e-3):
+    """Central difference of f(x) = Re <g, A x> along v against <grad, v> (the map is linear,
+    so the quotient is exact up to rounding for any step)."""
+    dY = (fm.apply(A, gpu(X + eps * v)) - fm.apply(A, gpu(X - eps * v))).to(torch.complex128)
+    fd = torch.vdot(g.flatten().to(torch.complex128), dY.flatten()).real.item() / (2 * eps)
+    an = float(np.real(np.vdot(grad.astype(np.complex128).ravel(), v.astype(np.complex128).ravel())))
+    assert abs(fd - an) <= tol * abs(an), (fd, an)
+
+
+def test_autograd_cs_operator_full_size(fm):
+    # config 2: Phi = P Diag(d) C at n = 2^18 on 64 complex64 columns, through the calibrated
+    # two-pass plan the benchmark times; gradient against the FP64 oracle's Phi^H g and central
+    # differences
+    c, d, idx, X, Y, G = I.cs_operator()
+    n = len(c)
+    A = fm.product(fm.partial(idx, n), fm.diag(d), fm.circulant(c))
+    A.calibrate(X.shape[0], torch.complex64)
+    x = gpu(X).requires_grad_(True)
+    g = gpu(G)
+    (fm.apply(A, x) * g.conj()).real.sum().backward()
+    ref = O.Product(O.Partial(idx, n), O.Diag(d), O.Circulant(c))
+    want = ref.apply(G.T, adjoint=True).T
+    got = x.grad.cpu().numpy()
+    assert colerr(got, want) <= tol32(n)
+    v = blk(X.shape[0], n, np.complex64)
+    _fd_check(fm, A, X, g, got, v)
+
+
+def test_autograd_real_input_complex_operator(fm):
+    # real x into a complex operator: the gradient is Re(A^H g), computed by the library
+    # (fm_backward with a real output type)
+    c, d, idx, X, Y, G = I.cs_operator(log2n=12, k=3)
+    n = len(c)
+    A = fm.product(fm.partial(idx, n), fm.diag(d), fm.circulant(c))
+    Xr = np.ascontiguousarray(X.real).astype(np.float32)
+    x = gpu(Xr).requires_grad_(True)
+    g = gpu(G)
+    (fm.apply(A, x) * g.conj()).real.sum().backward()
+    assert x.grad.dtype == torch.float32
+    ref = O.Product(O.Partial(idx, n), O.Diag(d), O.Circulant(c))
+    want = ref.apply(G.T, adjoint=True).T.real
+    assert colerr(x.grad.cpu().numpy(), want) <= tol32(n)
+    assert torch.equal(x.grad, A.backward(g, real_out=True))
+
+
+def test_autograd_kron_analogue(fm):
+    # config 4's 2^12 analogue Kron(H_16, C_16, F_16): gradient against the oracle's A^H g and
+    # central differences (the adjoint recomputes the mode-product intermediates)
+    c, X, Y = I.kron_small()
+    A = fm.kron(fm.hadamard(4), fm.circulant(c), fm.fourier(16))
+    ref = O.Kron(O.Hadamard(16), O.Circulant(c), O.Fourier(16))
+    Xc = X.astype(np.complex64)
+    x = gpu(Xc).requires_grad_(True)
+    G = blk(X.shape[0], 4096, np.complex64)
+    g = gpu(G)
+    (fm.apply(A, x) * g.conj()).real.sum().backward()
+    want = ref.apply(G.T.astype(np.complex128), adjoint=True).T
+    got = x.grad.cpu().numpy()
+    assert colerr(got, want) <= tol32(4096)
+    _fd_check(fm, A, Xc, g, got, blk(X.shape[0], 4096, np.complex64))
+
+
+def test_autograd_kron_full_size(fm):
+    # config 4 at full size, 2^24 x 4: the gradient is the library adjoint of g, and central
+    # differences along a random direction agree with it
+    c, X, Y = I.kron_large()
+    A = fm.kron(fm.hadamard(8), fm.circulant(c), fm.fourier(64))
+    x = gpu(X).requires_grad_(True)
+    g = gpu(Y)
+    (fm.apply(A, x) * g.conj()).real.sum().backward()
+    assert torch.equal(x.grad, A.backward(g))
+    v = I.cn(np.random.default_rng(41), X.shape, np.complex64)
+    _fd_check(fm, A, X, g, x.grad.cpu().numpy(), v, tol=2e-3)
+
+
+def test_autograd_hadamard_fd_slice(fm):
+    # config 1: central differences on the first 2^10 input coordinates of column 0 -- along a
+    # random direction supported on that slice, and along e_j for a spread of j in it
+    n = 1 << 16
+    X = blk(4, n, np.float32)
+    A = fm.hadamard(16)
+    x = gpu(X).requires_grad_(True)
+    G = blk(4, n, np.float32)
+    (fm.apply(A, x) * gpu(G)).sum().backward()
+    grad = x.grad.cpu().numpy()
+    gd = gpu(G).to(torch.float64)
+    rng = np.random.default_rng(5)
+    v = np.zeros_like(X)
+    v[0, :1024] = rng.standard_normal(1024)
+    dY = (fm.apply(A, gpu(X + 0.5 * v)) - fm.apply(A, gpu(X - 0.5 * v))).to(torch.float64)
+    fd = (dY * gd).sum().item()
+    an = float(np.dot(grad[0, :1024].astype(np.float64), v[0, :1024]))
+    assert abs(fd - an) <= 1e-3 * abs(an)
+    for j in range(0, 1024, 73):
+        e = np.zeros_like(X)
+        e[0, j] = 0.5
+        dY = (fm.apply(A, gpu(X + e)) - fm.apply(A, gpu(X - e))).to(torch.float64)
+        assert abs((dY * gd).sum().item() - grad[0, j]) <= 1e-3 * max(1.0, abs(grad[0, j]))
+
+
 # ---------------------------------------------------------------- edge cases
 def test_zero_columns_and_strided_input(fm):
     A = fm.fourier(64)

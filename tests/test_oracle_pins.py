@@ -66,6 +66,21 @@ def test_golden_toeplitz3():
     assert np.allclose(T.apply(g["x"], adjoint=True), g["yadj"])
 
 
+def _lasso_cases():
+    g = _kv("lasso_toeplitz2.txt")
+    return [(O.Toeplitz(g["sq_t"], 2, 2), g["sq_b"], g["sq_x"], float(g["sq_lam"][0]), float(g["sq_objective"][0]),
+             float(g["sq_lambda"][0])),
+            (O.Toeplitz(g["re_t"], 2, 3), g["re_b"], g["re_x"], float(g["re_lam"][0]), float(g["re_objective"][0]),
+             float(g["re_lambda"][0]))]
+
+
+def test_golden_lasso_objective_and_lambda():
+    # objective = 1/2 ||A x - b||^2 + lam ||x||_1 and lambda = 0.01 ||A^T b||_inf, worked by hand
+    for A, b, x, lam, obj, lam_b in _lasso_cases():
+        assert abs(O.objective(A, b, x, lam) - obj) <= 1e-12 * obj
+        assert abs(O.lambda_from_b(A, b) - lam_b) <= 1e-12 * lam_b
+
+
 # ----------------------------------------------------------------- Fourier, Eq. (1)
 @pytest.mark.parametrize("n", [1, 2, 3, 8, 12, 64, 256])
 def test_fourier_dense_matches_library_dft(n):
@@ -396,6 +411,32 @@ class _ToeplitzOffByOne(O.Toeplitz):
 class _KronSwapped(O.Kron):
     def dense(self):                                    # factors in the wrong order
         return O.Kron(*self.factors[::-1]).dense()
+
+
+def _objective_no_half(A, b, x, lam):                  # drops the 1/2 of the data term
+    r = A.apply(x) - b
+    return float(np.vdot(r, r).real) + lam * float(np.sum(np.abs(x)))
+
+
+def _objective_l2(A, b, x, lam):                       # 2-norm in place of the l1 norm
+    r = A.apply(x) - b
+    return 0.5 * float(np.vdot(r, r).real) + lam * float(np.linalg.norm(x))
+
+
+def _lambda_forward(A, b, rel=0.01):                   # A b in place of A^T b
+    return rel * float(np.max(np.abs(A.apply(b))))
+
+
+def _lambda_two_norm(A, b, rel=0.01):                  # 2-norm in place of the max norm
+    return rel * float(np.linalg.norm(A.apply(b, adjoint=True)))
+
+
+def test_planted_lasso_mistakes_are_caught():
+    (A, b, x, lam, obj, lam_b), _ = _lasso_cases()
+    for wrong in (_objective_no_half, _objective_l2):
+        assert abs(wrong(A, b, x, lam) - obj) > 1e-6
+    for wrong in (_lambda_forward, _lambda_two_norm):
+        assert abs(wrong(A, b) - lam_b) > 1e-6
 
 
 def test_planted_mistakes_are_caught():

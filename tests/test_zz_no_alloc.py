@@ -43,11 +43,37 @@ def test_noalloc_matches_ordinary_entry_points(fm):
         X = torch.from_numpy((rng.standard_normal((k, n)) + 1j * rng.standard_normal((k, n)))
                              .astype(np.complex64)).cuda()
         want = C.backward(X) if adjoint else C.forward(X)
-        for _ in range(2):                 # two calls in a row share the static scratch
-            Y = torch.full_like(X, float("nan"))
+        Ys = [torch.full_like(X, float("nan")) for _ in range(2)]
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
+        for Y in Ys:                       # two calls in a row share the static scratch
             _lib.fm_circulant_apply_noalloc(C.handle, adjoint, X.data_ptr(), n, Y.data_ptr(), n, k, stream)
-            torch.cuda.synchronize()
+        torch.cuda.synchronize()
+        # the calls reserved nothing on the device: the static array was set up when the
+        # operator was built, and no workspace was grown
+        assert torch.cuda.mem_get_info()[0] == free_before
+        for Y in Ys:
             assert _relerr(Y, want) <= tol
+
+
+def test_noalloc_largest_call_and_leading_dimensions(fm):
+    from paper_1710_09578_gb300 import _lib
+    rng = np.random.default_rng(12)
+    n, k = 1 << 18, 8                      # exactly the 16 MiB the static scratch holds
+    c = rng.standard_normal(n).astype(np.float32)
+    C = fm.circulant(c)
+    ldx, ldy = n + 64, n + 128             # leading dimensions larger than the column length
+    Xb = torch.from_numpy((rng.standard_normal((k, ldx)) + 1j * rng.standard_normal((k, ldx)))
+                          .astype(np.complex64)).cuda()
+    X = Xb[:, :n]
+    want = C.forward(X)
+    Yb = torch.full((k, ldy), float("nan"), dtype=torch.complex64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    for _ in range(2):
+        _lib.fm_circulant_apply_noalloc(C.handle, 0, Xb.data_ptr(), ldx, Yb.data_ptr(), ldy, k, stream)
+        torch.cuda.synchronize()
+        assert _relerr(Yb[:, :n], want) <= 1e-5 * np.log2(n)
+    assert torch.isnan(Yb[:, n:].real).all()   # nothing written between the columns
 
 
 def test_noalloc_rejects_oversized_calls(fm):
