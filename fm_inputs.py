@@ -27,6 +27,7 @@ __all__ = [
     "cs_operator",
     "fista_instance",
     "fista_measurements",
+    "kron_generator",
     "kron_large",
     "kron_small",
     "column_block",
@@ -127,6 +128,11 @@ def fista_measurements(inst: dict, snr_db: float = 30.0) -> np.ndarray:
     clean = ent @ x0[supp]
     noise = g * (np.linalg.norm(clean) / np.linalg.norm(g)) * 10.0 ** (-snr_db / 20.0)
     return (clean + noise).astype(np.float32)
+
+
+def kron_generator(seed: int = 4, n_c: int = 1024) -> np.ndarray:
+    """The circulant generator of the Kron workload alone (the first draw of its stream)."""
+    return cn(np.random.default_rng(seed), (n_c,))
 
 
 def kron_large(k: int = 4, seed: int = 4, n_c: int = 1024, n_total: int = 1 << 24,

@@ -280,6 +280,24 @@ fm_status fm_batch_sizes(fm_batch B, int64_t* total_rows, int64_t* total_cols);
 fm_status fm_fista_batch(fm_batch B, const float* b, float* x, float* y, const fm_fista_params* p,
                          const fm_fista_report* rep, void* stream);
 
+/* ---------------------------------------------------------------- tracing */
+
+/* Device time of the library's kernels (profiling; the paper has no counterpart).  Between
+ * fm_trace_begin and fm_trace_end every kernel the library launches, on any stream and from
+ * any thread, is bracketed by two CUDA events recorded on its stream, up to max_launches
+ * launches (later launches run untraced).  An event between two kernels ends the early start
+ * of programmatic dependent launch, so traced kernels run one after another.  fm_trace_begin
+ * creates the events (host resources, no device memory) and fails if tracing is already on.
+ * fm_trace_end waits for the traced launches, copies the first max_entries of them (kernel
+ * label, milliseconds) in launch order to out (host, may be NULL), sets *n_entries (may be
+ * NULL) to the number of launches seen while tracing was on, and frees the events. */
+typedef struct {
+  char kernel[64]; /* kernel label, e.g. "fft2_kernel<f32,L=2^10,strided,conv>" */
+  float ms;        /* device time between the launch's two events */
+} fm_trace_entry;
+fm_status fm_trace_begin(int32_t max_launches);
+fm_status fm_trace_end(fm_trace_entry* out, int32_t max_entries, int32_t* n_entries);
+
 /* ---------------------------------------------------------------- misc */
 
 void fm_release(fm_op A);

@@ -38,6 +38,10 @@ class fm_fista_report(ctypes.Structure):
                 ("objective", ctypes.c_void_p), ("status", ctypes.c_void_p)]
 
 
+class fm_trace_entry(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_char * 64), ("ms", ctypes.c_float)]
+
+
 class fm_tune_entry(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int64), ("n1", ctypes.c_int64), ("ncand", ctypes.c_int32),
                 ("cand_n1", ctypes.c_int64 * 8), ("ms", ctypes.c_float * 8)]
@@ -79,6 +83,8 @@ _SIGS = {
     "fm_fista_batch": [_p, _p, _p, _p, ctypes.POINTER(fm_fista_params), ctypes.POINTER(fm_fista_report), _p],
     "fm_calibrate": [_op, _i64, _i32, _p, ctypes.POINTER(fm_tune_entry), _i32, ctypes.POINTER(_i32)],
     "fm_set_split": [_op, _i64, _i64, _p],
+    "fm_trace_begin": [_i32],
+    "fm_trace_end": [ctypes.POINTER(fm_trace_entry), _i32, ctypes.POINTER(_i32)],
 }
 for _name, _args in _SIGS.items():
     getattr(lib, _name).argtypes = _args
@@ -239,6 +245,18 @@ def fm_fista_batch(b, b_ptr: int, x_ptr: int, y_ptr: int | None, params: fm_fist
                    report: fm_fista_report | None, stream: int = 0):
     rep = ctypes.byref(report) if report is not None else None
     check(lib.fm_fista_batch(b, b_ptr, x_ptr, y_ptr, ctypes.byref(params), rep, stream), "fm_fista_batch")
+
+
+def fm_trace_begin(max_launches: int):
+    check(lib.fm_trace_begin(max_launches), "fm_trace_begin")
+
+
+def fm_trace_end(max_entries: int = 1 << 16):
+    """Stop tracing; returns [(kernel label, ms), ...] in launch order."""
+    buf = (fm_trace_entry * max_entries)()
+    n = _i32(0)
+    check(lib.fm_trace_end(buf, max_entries, ctypes.byref(n)), "fm_trace_end")
+    return [(e.kernel.decode(errors="replace"), float(e.ms)) for e in buf[:min(n.value, max_entries)]]
 
 
 def fm_release(h):

@@ -423,7 +423,11 @@ fm_status fft2_start(const FftArgs<T>& a, int64_t tiles, size_t smem, cudaStream
     if (e != cudaSuccess) { set_error("fft smem attribute: %s", cudaGetErrorString(e)); return FM_ERR_CUDA; }
     attr_bytes[dev].store(smem);
   }
-  return pdl_go("fft2_kernel", kern, dim3((unsigned)tiles), dim3(THREADS), smem, st, a);
+  // the kernel's label in errors and traces: element type, length, layout, convolution
+  static const std::string label = std::string("fft2_kernel<") + (sizeof(T) == 4 ? "f32" : "f64") + ",L=2^" +
+                                   std::to_string(LOGL) + (VF ? ",strided" : "") + (SIMPLE ? "" : ",fused") +
+                                   (CONV ? ",conv" : "") + ">";
+  return pdl_go(label.c_str(), kern, dim3((unsigned)tiles), dim3(THREADS), smem, st, a);
 }
 
 template <typename T, int LOGL, int THREADS, int EPT, bool VF>

@@ -713,7 +713,9 @@ static fm_status fista_run(fm_batch B, const float* b, float* x, const float* co
     a.single_group = -1;
     FM_CUDA(cudaMemsetAsync(B->counter, 0, sizeof(int), st));
     const int grid = std::min(B->ngroups, B->sms);
+    const int ts = g_trace_on.load(std::memory_order_relaxed) ? trace_open(st) : -1;
     fista_kernel<<<grid, kFThreads, smem, st>>>(a);
+    if (ts >= 0) trace_close(ts, st, "fista_kernel");
     return after_launch("fista_kernel");
   }
   // one instance per launch, in the caller's order
@@ -721,7 +723,9 @@ static fm_status fista_run(fm_batch B, const float* b, float* x, const float* co
   a.ngroups = B->nsingle;
   for (int64_t i = 0; i < B->count; ++i) {
     a.single_group = B->single_index[i];
+    const int ts = g_trace_on.load(std::memory_order_relaxed) ? trace_open(st) : -1;
     fista_kernel<<<1, kFThreads, smem, st>>>(a);
+    if (ts >= 0) trace_close(ts, st, "fista_kernel");
     FM_TRY(after_launch("fista_kernel"));
   }
   return FM_OK;

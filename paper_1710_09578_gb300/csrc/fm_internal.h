@@ -66,10 +66,18 @@ inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kern, args...);
 }
+// Launch tracing (trace.cu): while fm_trace_begin is in effect, trace_open records a start
+// event on the launch's stream (returns its slot, or -1) and trace_close the end event.
+extern std::atomic<int> g_trace_on;
+int trace_open(cudaStream_t st);
+void trace_close(int slot, cudaStream_t st, const char* name);
+
 template <typename... KArgs, typename... Args>
 inline fm_status pdl_go(const char* what, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
                         cudaStream_t st, Args... args) {
+  const int ts = g_trace_on.load(std::memory_order_relaxed) ? trace_open(st) : -1;
   cudaError_t e = launch_pdl(kern, grid, block, smem, st, args...);
+  if (ts >= 0) trace_close(ts, st, what);
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
     set_error("launch of %s failed: %s", what, cudaGetErrorString(e));

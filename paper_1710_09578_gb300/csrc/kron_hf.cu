@@ -105,7 +105,8 @@ fm_status hf_start(const KronHFArgs& a, cudaStream_t st) {
   }
   if (a.ntiles == 0) return FM_OK;
   if (a.ntiles > 0x7fffffffLL) { set_error("kron_hf: too many tiles"); return FM_ERR_UNSUPPORTED; }
-  return pdl_go("kron_hf_kernel", kern, dim3((unsigned)a.ntiles), dim3(1 << (LA + LB - 4)), smem, st, a);
+  static const std::string label = "kron_hf_kernel<" + std::to_string(LA) + "," + std::to_string(LB) + ">";
+  return pdl_go(label.c_str(), kern, dim3((unsigned)a.ntiles), dim3(1 << (LA + LB - 4)), smem, st, a);
 }
 
 }  // namespace

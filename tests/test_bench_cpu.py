@@ -20,6 +20,6 @@ def test_reference_arm_json_line():
               "scaling", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert k in d, k
     assert d["value"] > 0 and d["unit"] == "GB/s" and d["higher_is_better"] is True
-    assert d["config"]["n"] == 1 << 16 and d["config"]["columns"] == 256
+    assert d["config"]["n"] == 1 << 24 and d["config"]["columns"] == 4
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]

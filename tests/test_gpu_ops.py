@@ -642,3 +642,24 @@ def test_repeat_calls_bit_identical(fm):
     a = A.forward(X)
     b = A.forward(X)
     assert torch.equal(a, b)
+
+
+# ---------------------------------------------------------------- launch tracing
+def test_trace_labels_and_times(fm):
+    from paper_1710_09578_gb300 import _lib
+    c, X, _ = I.kron_small()
+    A = fm.kron(fm.hadamard(8), fm.circulant(np.tile(c, 4)), fm.fourier(64))
+    Xg = gpu(blk(2, A.cols, np.complex64))
+    A.forward(Xg)
+    torch.cuda.synchronize()
+    _lib.fm_trace_begin(16)
+    before = fm.launch_count()
+    A.forward(Xg)
+    A.backward(Xg)
+    recs = _lib.fm_trace_end()
+    assert len(recs) == fm.launch_count() - before == 4      # two passes per apply
+    names = [r[0] for r in recs]
+    assert names[0].startswith("kron_hf_kernel<8,6>") and names[1].startswith("fft2_kernel<f32,L=2^6,strided,conv>")
+    assert all(ms > 0 for _, ms in recs)
+    with pytest.raises(fm.FmError):
+        _lib.fm_trace_end()                                   # not on any more
