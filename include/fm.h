@@ -179,6 +179,26 @@ fm_status fm_reserve(fm_op A, int64_t ncols, fm_dtype xdt, void* stream);
 fm_status fm_circulant_apply_noalloc(fm_op C, int adjoint, const void* X, int64_t ldx, void* Y, int64_t ldy,
                                      int64_t ncols, void* stream);
 
+/* Gradient with respect to the parameter vector of `leaf` (Sec. 2.1.1: operators built from
+ * parameter vectors), for a real loss of Y = A X with upstream gradient G = dloss/dconj(Y) (the
+ * convention of fm_backward: the gradient of X is A^H G).  leaf is a Diag (parameter d, n
+ * entries), Circulant (first column c, n entries) or Toeplitz (generator t = [first column;
+ * first row without t0], rows + cols - 1 entries) operator that is A itself or appears once,
+ * not as an adjoint, among the terms of A's (nested) product.  Y is bilinear in (theta, X), so
+ *   grad[k] = sum over columns and over the entries (i, j) of the leaf holding theta_k of
+ *             G_leaf[i] conj(Z[j]),
+ * the real part for a real leaf, where Z is the leaf's input (the terms applied before it,
+ * recomputed from X; nothing of the forward pass is stored) and G_leaf the gradient at its
+ * output (the adjoints of the terms applied after it, applied to G).  For a circulant or
+ * Toeplitz leaf the sum is the circular correlation (1/L) F^H sum_c (F G_leaf) conj(F Z) of the
+ * columns zero-padded to the leaf's transform length L.
+ * X: cols(A) x ncols (dtype xdt in F32, F64, C64, C128, leading dimension ldx), G: rows(A) x
+ * ncols of dtype fm_out_dtype(A, xdt) (ldg), grad: device vector of the parameter length, of
+ * dtype complex_of(xdt) for a complex leaf and the real type of xdt's precision for a real
+ * one; it is overwritten.  Intermediates come from A's workspace (grown on demand). */
+fm_status fm_param_grad(fm_op A, fm_op leaf, const void* X, int64_t ldx, fm_dtype xdt, const void* G, int64_t ldg,
+                        fm_dtype gdt, int64_t ncols, void* grad, fm_dtype grad_dt, void* stream);
+
 /* ---------------------------------------------------------------- calibration */
 
 /* Calibration of the execution plan: the GPU form of the paper's calibration step

@@ -21,7 +21,8 @@ from ._lib import (FM_HAD_BF16, FM_HAD_BF16X2, FM_HAD_FP32, FM_HAD_INT8, FmError
                    fm_fista_params, fm_fista_report)
 
 __all__ = ["Op", "fourier", "circulant", "toeplitz", "hadamard", "diag", "partial", "product",
-           "sum_", "blkdiag", "kron", "FmApply", "apply", "FistaBatch", "fista", "FmError",
+           "sum_", "blkdiag", "kron", "FmApply", "apply", "param_grad", "FmParamApply", "apply_params",
+           "FistaBatch", "fista", "FmError",
            "FM_HAD_FP32", "FM_HAD_BF16", "FM_HAD_BF16X2", "FM_HAD_INT8", "launch_count"]
 
 _TORCH2FM = {torch.int8: _lib.FM_I8, torch.int32: _lib.FM_I32, torch.float32: _lib.FM_F32,
@@ -59,9 +60,10 @@ def _param(x, allow_int=False):
 class Op:
     """An immutable structured operator (handle to the C library)."""
 
-    def __init__(self, handle: int, kids=()):
+    def __init__(self, handle: int, kids=(), kind: str = ""):
         self._h = handle
         self._kids = tuple(kids)  # composites also hold C references; kept for clarity
+        self.kind = kind
         self.rows, self.cols = _lib.fm_shape(handle)
         self.real = _lib.fm_is_real(handle)
 
@@ -176,7 +178,7 @@ def fourier(n: int, ortho: bool = False) -> Op:
 
 def circulant(c) -> Op:
     p, dt, keep = _param(c)
-    return Op(_lib.fm_circulant(p, len(keep), dt, _stream()))
+    return Op(_lib.fm_circulant(p, len(keep), dt, _stream()), kind="circulant")
 
 
 def toeplitz(t, rows: int, cols: int | None = None) -> Op:
@@ -184,7 +186,7 @@ def toeplitz(t, rows: int, cols: int | None = None) -> Op:
     p, dt, keep = _param(t)
     if len(keep) != rows + cols - 1:
         raise ValueError("t must hold rows + cols - 1 entries")
-    return Op(_lib.fm_toeplitz(p, rows, cols, dt, _stream()))
+    return Op(_lib.fm_toeplitz(p, rows, cols, dt, _stream()), kind="toeplitz")
 
 
 def hadamard(log2n: int, mode: int = FM_HAD_FP32) -> Op:
@@ -193,7 +195,7 @@ def hadamard(log2n: int, mode: int = FM_HAD_FP32) -> Op:
 
 def diag(d) -> Op:
     p, dt, keep = _param(d)
-    return Op(_lib.fm_diag(p, len(keep), dt, _stream()))
+    return Op(_lib.fm_diag(p, len(keep), dt, _stream()), kind="diag")
 
 
 def partial(idx, n: int) -> Op:
@@ -242,6 +244,66 @@ class FmApply(torch.autograd.Function):
 def apply(op: Op, X: torch.Tensor) -> torch.Tensor:
     """Differentiable A X."""
     return FmApply.apply(X, op)
+
+
+def param_grad(A: Op, leaf: Op, X: torch.Tensor, G: torch.Tensor) -> torch.Tensor:
+    """Gradient with respect to the parameter vector of `leaf` (a Diag, Circulant or Toeplitz
+    term of A) for Y = A X and upstream gradient G = dloss/dconj(Y) (``fm_param_grad``).
+    X: [K, cols(A)], G: [K, rows(A)]; returns a vector of the parameter length, complex for a
+    complex leaf and real for a real one."""
+    X2 = (X.unsqueeze(0) if X.dim() == 1 else X).contiguous()
+    G2 = (G.unsqueeze(0) if G.dim() == 1 else G).contiguous()
+    if X2.shape[0] != G2.shape[0] or X2.shape[1] != A.cols or G2.shape[1] != A.rows:
+        raise ValueError("X must be [K, cols(A)] and G [K, rows(A)]")
+    dbl = X2.dtype in (torch.float64, torch.complex128)
+    if leaf.real:
+        gdt = torch.float64 if dbl else torch.float32
+    else:
+        gdt = torch.complex128 if dbl else torch.complex64
+    plen = leaf.rows + leaf.cols - 1 if leaf.kind == "toeplitz" else leaf.rows
+    out = torch.empty(plen, dtype=gdt, device=X2.device)
+    _lib.fm_param_grad(A.handle, leaf.handle, X2.data_ptr(), X2.shape[1], _TORCH2FM[X2.dtype], G2.data_ptr(),
+                       G2.shape[1], _TORCH2FM[G2.dtype], X2.shape[0], out.data_ptr(), _TORCH2FM[gdt], _stream())
+    return out
+
+
+class FmParamApply(torch.autograd.Function):
+    """y = A(params) x, differentiable in x and in the parameter vectors.
+
+    ``build(*params)`` returns (A, leaves) with leaves[i] the Diag / Circulant / Toeplitz
+    operator made from params[i].  Only x is saved: the backward recomputes the intermediates
+    the parameter gradients need inside the library (``fm_param_grad``).
+    """
+
+    @staticmethod
+    def forward(ctx, X, build, *params):
+        A, leaves = build(*[p.detach() for p in params])
+        ctx.A, ctx.leaves = A, list(leaves)
+        ctx.real_in = not X.is_complex()
+        ctx.pdtypes = [p.dtype for p in params]
+        ctx.save_for_backward(X)
+        return A.forward(X)
+
+    @staticmethod
+    def backward(ctx, g):
+        (X,) = ctx.saved_tensors
+        g = g.contiguous()
+        gx = ctx.A.backward(g, real_out=ctx.real_in) if ctx.needs_input_grad[0] else None
+        gps = []
+        for i, leaf in enumerate(ctx.leaves):
+            if not ctx.needs_input_grad[2 + i]:
+                gps.append(None)
+                continue
+            gp = param_grad(ctx.A, leaf, X, g)
+            if not ctx.pdtypes[i].is_complex and gp.is_complex():
+                gp = gp.real
+            gps.append(gp.to(ctx.pdtypes[i]))
+        return (gx, None, *gps)
+
+
+def apply_params(build, X: torch.Tensor, *params: torch.Tensor) -> torch.Tensor:
+    """Differentiable A(params) X: see FmParamApply."""
+    return FmParamApply.apply(X, build, *params)
 
 
 # ---------------------------------------------------------------- FISTA

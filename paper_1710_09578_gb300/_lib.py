@@ -83,6 +83,7 @@ _SIGS = {
     "fm_fista_batch": [_p, _p, _p, _p, ctypes.POINTER(fm_fista_params), ctypes.POINTER(fm_fista_report), _p],
     "fm_calibrate": [_op, _i64, _i32, _p, ctypes.POINTER(fm_tune_entry), _i32, ctypes.POINTER(_i32)],
     "fm_set_split": [_op, _i64, _i64, _p],
+    "fm_param_grad": [_op, _op, _p, _i64, _i32, _p, _i64, _i32, _i64, _p, _i32, _p],
     "fm_trace_begin": [_i32],
     "fm_trace_end": [ctypes.POINTER(fm_trace_entry), _i32, ctypes.POINTER(_i32)],
 }
@@ -245,6 +246,11 @@ def fm_fista_batch(b, b_ptr: int, x_ptr: int, y_ptr: int | None, params: fm_fist
                    report: fm_fista_report | None, stream: int = 0):
     rep = ctypes.byref(report) if report is not None else None
     check(lib.fm_fista_batch(b, b_ptr, x_ptr, y_ptr, ctypes.byref(params), rep, stream), "fm_fista_batch")
+
+
+def fm_param_grad(h, leaf, X: int, ldx: int, xdt: int, G: int, ldg: int, gdt: int, ncols: int, grad: int,
+                  grad_dt: int, stream: int = 0):
+    check(lib.fm_param_grad(h, leaf, X, ldx, xdt, G, ldg, gdt, ncols, grad, grad_dt, stream), "fm_param_grad")
 
 
 def fm_trace_begin(max_launches: int):

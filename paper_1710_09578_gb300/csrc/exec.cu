@@ -850,6 +850,25 @@ void free_big_plan(BigPlan* plan) {
   plan->L = 0;
 }
 
+fm_status exec_dft(int64_t L, const BigPlan* big, int dir, const View& in, int64_t lin, const View& out,
+                   int64_t ncols, double scale, Ctx& ctx) {
+  if (!is_complex(in.dt) || in.dt != out.dt) {
+    set_error("exec_dft: complex views of one precision expected");
+    return FM_ERR_DTYPE;
+  }
+  FftJob J;
+  J.L = L;
+  J.big = big && big->L == L ? big : nullptr;
+  J.conv = 0;
+  J.dir = dir;
+  J.Lin = lin;
+  J.Lout = L;
+  J.scale = scale;
+  J.real = false;
+  return is_double(in.dt) ? run_fft<double>(J, Fused(), in, out, ncols, 0, ctx)
+                          : run_fft<float>(J, Fused(), in, out, ncols, 0, ctx);
+}
+
 fm_status construction_fft64(const double2* in, double2* out, int64_t L, const BigPlan* big, cudaStream_t st) {
   int dev = 0;
   FM_CUDA(cudaGetDevice(&dev));

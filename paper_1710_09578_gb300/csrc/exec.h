@@ -32,6 +32,12 @@ struct Ctx {
 fm_status natural_out_dtype(const fm_op_s* A, fm_dtype in, fm_dtype* out);
 fm_status exec(const fm_op_s* A, bool adj, const View& in, const View& out, int64_t ncols, int beta, Ctx& ctx);
 
+// Unscaled DFT of length L (dir -1: F, +1: F^H) of ncols packed columns, times `scale`;
+// the input columns hold lin <= L entries (zero-padded to L on load).  Complex views, FP32
+// or FP64 after their dtype; `big` is the two-pass plan of L when L is longer than a tile.
+fm_status exec_dft(int64_t L, const BigPlan* big, int dir, const View& in, int64_t lin, const View& out,
+                   int64_t ncols, double scale, Ctx& ctx);
+
 // Single-column FP64 DFT used at construction (spectra): out = F x (dir -1) of length L.
 fm_status construction_fft64(const double2* in, double2* out, int64_t L, const BigPlan* big, cudaStream_t st);
 fm_status make_big_plan(int64_t L, BigPlan* plan, cudaStream_t st);

@@ -14,6 +14,7 @@ import pytest
 import scipy.linalg as sla
 
 import oracle as O
+import oracle.gradients as OG
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 RNG = np.random.default_rng(1234)
@@ -391,6 +392,91 @@ def test_ista_monotone_and_resume():
     x1, st = O.fista(A, b, lam, L, iters=13, return_state=True)
     x2 = O.fista(A, b, lam, L, iters=17, state=st)
     assert np.array_equal(x2, O.fista(A, b, lam, L, iters=30))
+
+
+# ----------------------------------------------------------------- parameter gradients
+def test_golden_param_grads():
+    g = _kv("param_grads2.txt")
+    x, gg = g["x"], g["g"]
+    assert np.allclose(OG.grad_diag(x, gg, real=True), g["grad_d"])
+    for f in (OG.grad_circulant, OG.grad_circulant_definition):
+        assert np.allclose(f(x, gg, real=True), g["grad_c"])
+    for f in (OG.grad_toeplitz, OG.grad_toeplitz_definition):
+        assert np.allclose(f(x, gg, 2, 2, real=True), g["grad_t"])
+
+
+@pytest.mark.parametrize("rows,cols", [(5, 5), (4, 7), (9, 3), (1, 4)])
+def test_param_grad_fast_routes_match_definitions(rows, cols):
+    X, G = crand(cols, 3), crand(rows, 3)
+    assert rel(OG.grad_toeplitz(X, G, rows, cols), OG.grad_toeplitz_definition(X, G, rows, cols)) < 1e-12
+    Xc, Gc = crand(8, 3), crand(8, 3)
+    assert rel(OG.grad_circulant(Xc, Gc), OG.grad_circulant_definition(Xc, Gc)) < 1e-12
+
+
+def _loss(A, X, G):
+    return float(np.real(np.vdot(G, A.apply(X))))
+
+
+@pytest.mark.parametrize("kind", ["diag", "circulant", "toeplitz"])
+@pytest.mark.parametrize("cplx", [False, True])
+def test_param_grads_match_central_differences(kind, cplx):
+    # loss(theta) = Re <G, A(theta) X> is linear in theta: central differences are exact up to
+    # rounding; for a complex parameter the real and imaginary directions give Re and Im of
+    # the gradient (d loss = Re <grad, d theta>)
+    rng = np.random.default_rng(3)
+    n, m = 8, 6
+    mk = {"diag": lambda p: O.Diag(p), "circulant": lambda p: O.Circulant(p),
+          "toeplitz": lambda p: O.Toeplitz(p, m, n)}[kind]
+    plen = {"diag": n, "circulant": n, "toeplitz": m + n - 1}[kind]
+    rows = m if kind == "toeplitz" else n
+    p0 = rng.standard_normal(plen) + (1j * rng.standard_normal(plen) if cplx else 0)
+    X, G = crand(n, 2), crand(rows, 2)
+    grad = OG.leaf_param_grad(mk(p0), X, G)
+    eps = 0.5
+    for k in range(plen):
+        for unit in ([1.0, 1j] if cplx else [1.0]):
+            e = np.zeros(plen, dtype=complex if cplx else float)
+            e[k] = unit
+            fd = (_loss(mk(p0 + eps * e), X, G) - _loss(mk(p0 - eps * e), X, G)) / (2 * eps)
+            an = np.real(np.conj(unit) * grad[k])
+            assert abs(fd - an) <= 1e-10 * max(1.0, abs(an))
+
+
+def test_product_param_grad_matches_central_differences():
+    # Phi = P Diag(d) C(c): gradients of d and c through the recomputed intermediates
+    rng = np.random.default_rng(4)
+    n, m = 16, 5
+    c = rng.standard_normal(n)
+    d = np.exp(2j * np.pi * rng.random(n))
+    idx = np.sort(rng.choice(n, m, replace=False))
+    build = lambda d_, c_: O.Product(O.Partial(idx, n), O.Diag(d_), O.Circulant(c_))  # noqa: E731
+    X, G = crand(n, 3), crand(m, 3)
+    gd = OG.product_param_grad(build(d, c), 1, X, G)
+    gc = OG.product_param_grad(build(d, c), 2, X, G)
+    v = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    fd = (_loss(build(d + 0.5 * v, c), X, G) - _loss(build(d - 0.5 * v, c), X, G))
+    assert abs(fd - np.real(np.vdot(gd, v))) < 1e-10 * abs(fd)
+    w = rng.standard_normal(n)
+    fd = (_loss(build(d, c + 0.5 * w), X, G) - _loss(build(d, c - 0.5 * w), X, G))
+    assert abs(fd - np.dot(gc, w)) < 1e-10 * abs(fd)
+    assert gc.dtype.kind == "f"
+
+
+def _grad_circulant_convolution(X, G, real=False):          # convolution instead of correlation
+    r = np.fft.ifft(np.sum(np.fft.fft(G, axis=0) * np.fft.fft(np.conj(X), axis=0), axis=1))
+    return r.real if real else r
+
+
+def test_planted_param_grad_mistakes_are_caught():
+    g = _kv("param_grads2.txt")
+    x, gg = g["x"][:, None], g["g"][:, None]
+    x3 = np.array([[1.0], [2.0], [5.0]])
+    g3 = np.array([[3.0], [4.0], [-1.0]])
+    assert not np.allclose(_grad_circulant_convolution(x3, g3, True), OG.grad_circulant_definition(x3, g3, True))
+    assert not np.allclose(OG.grad_diag(gg, x, True) * 0 + np.sum(gg * x), g["grad_d"])   # a summed, not per-entry, gradient
+    # Toeplitz with the row part read in the wrong order (t[rows + j - i] off by one)
+    bad = np.concatenate([OG.grad_toeplitz(x, gg, 2, 2, True)[:2], [np.sum(gg[0] * x[0])]])
+    assert not np.allclose(bad, g["grad_t"])
 
 
 # ----------------------------------------------------------------- planted mistakes
