@@ -27,6 +27,8 @@ __all__ = [
     "cs_operator",
     "fista_instance",
     "fista_measurements",
+    "ndt_model",
+    "compressed_rows",
     "kron_generator",
     "kron_large",
     "kron_small",
@@ -128,6 +130,26 @@ def fista_measurements(inst: dict, snr_db: float = 30.0) -> np.ndarray:
     clean = ent @ x0[supp]
     noise = g * (np.linalg.norm(clean) / np.linalg.norm(g)) * 10.0 ** (-snr_db / 20.0)
     return (clean + noise).astype(np.float32)
+
+
+def ndt_model(n1: int = 4, n2: int = 8, n3: int = 8, k: int = 3, seed: int = 5, dtype=np.complex64):
+    """Block model of Sec. 3: an n1 x n1 grid of two-level Toeplitz blocks with levels of
+    2 n2 - 1 and 2 n3 - 1 points (square blocks).  Draw order: the generators h[i][j]
+    ~ CN(0,1) of shape (2(2 n2 - 1) - 1) x (2(2 n3 - 1) - 1), row-major over (i, j); then
+    X ~ CN(0,1) [k, n1 (2 n2 - 1)(2 n3 - 1)] and Y the same."""
+    rng = np.random.default_rng(seed)
+    a, b = 2 * n2 - 1, 2 * n3 - 1
+    h = cn(rng, (n1, n1, 2 * a - 1, 2 * b - 1), dtype)
+    X = cn(rng, (k, n1 * a * b), dtype)
+    Y = cn(rng, (k, n1 * a * b), dtype)
+    return h, X, Y
+
+
+def compressed_rows(n_meas: int, n_t: int, n_f: int, seed: int = 6):
+    """Row selections of the compressed model (Eq. (9)): for each of n_meas pulse-echo signals
+    of n_t samples, n_f distinct Fourier rows, sorted (choice(n_t, n_f) per signal)."""
+    rng = np.random.default_rng(seed)
+    return [np.sort(rng.choice(n_t, size=n_f, replace=False)).astype(np.int32) for _ in range(n_meas)]
 
 
 def kron_generator(seed: int = 4, n_c: int = 1024) -> np.ndarray:

@@ -120,6 +120,27 @@ fm_status fm_blkdiag(const fm_op* blocks, int k, fm_op* out);
 fm_status fm_kron(const fm_op* factors, int k, fm_op* out);
 fm_status fm_hermitian(fm_op A, fm_op* out);
 
+/* Block matrix [B_ij] of nrows x ncols operators (the block arrangement of the ultrasound model
+ * H = [H_ij] of Sec. 3): blocks[i * ncols + j] is block (i, j); the blocks of one block row share
+ * their row count and those of one block column their column count (FM_ERR_SHAPE otherwise).
+ * Forward: output segment i = sum_j B_ij (input segment j); backward: segment j = sum_i
+ * B_ij^H (segment i).  Holds a reference to every block. */
+fm_status fm_blocks(const fm_op* blocks, int nrows, int ncols, fm_op* out);
+
+/* Two-level Toeplitz matrix (a 2-D non-cyclic convolution, the blocks H_ij of Sec. 3) of shape
+ * (r1 r2) x (c1 c2), vectors read as row-major r1 x r2 (output) and c1 x c2 (input) grids:
+ *   T2[(i1, i2), (j1, j2)] = t[k(i1, j1; r1) * (r2 + c2 - 1) + k(i2, j2; r2)],
+ *   k(i, j; r) = i - j for i >= j and r - 1 + j - i for i < j (the 1-D rule of fm_toeplitz on
+ *   each level), so t is a row-major (r1 + c1 - 1) x (r2 + c2 - 1) array (host or device).
+ * Built as Eq. (7) writes it: the zero-padding of the input to the L1 x L2 grid
+ * (L = 2^ceil(log2(r + c - 1)) per level), (F_L1 (x) F_L2)^H Diag(h) (F_L1 (x) F_L2) with
+ * h = (F_L1 (x) F_L2) e / (L1 L2) computed in FP64 from the embedded generator e, and the
+ * truncation to the r1 x r2 block: the handle returned is that Product.  It is complex (its
+ * output for a real generator and real input is real up to rounding: request the real type
+ * to keep the real part).  L1 L2 <= 2^24. */
+fm_status fm_toeplitz2(const void* t, int64_t r1, int64_t c1, int64_t r2, int64_t c2, fm_dtype dt, void* stream,
+                       fm_op* out);
+
 /* ---------------------------------------------------------------- queries */
 
 fm_status fm_shape(fm_op A, int64_t* rows, int64_t* cols);

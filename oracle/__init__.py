@@ -26,3 +26,4 @@ from .operators import (  # noqa: F401
     Product, Sum, BlkDiag, Kron, embedding_spectrum,
 )
 from .fista import soft, lipschitz, lambda_from_b, fista, objective, fista_problem  # noqa: F401
+from .ndt import Blocks, Toeplitz2  # noqa: F401

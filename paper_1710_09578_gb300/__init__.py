@@ -20,7 +20,8 @@ from . import _lib
 from ._lib import (FM_HAD_BF16, FM_HAD_BF16X2, FM_HAD_FP32, FM_HAD_INT8, FmError,  # noqa: F401
                    fm_fista_params, fm_fista_report)
 
-__all__ = ["Op", "fourier", "circulant", "toeplitz", "hadamard", "diag", "partial", "product",
+__all__ = ["Op", "fourier", "circulant", "toeplitz", "toeplitz2", "hadamard", "diag", "partial", "product",
+           "blocks",
            "sum_", "blkdiag", "kron", "FmApply", "apply", "param_grad", "FmParamApply", "apply_params",
            "FistaBatch", "fista", "FmError",
            "FM_HAD_FP32", "FM_HAD_BF16", "FM_HAD_BF16X2", "FM_HAD_INT8", "launch_count"]
@@ -187,6 +188,28 @@ def toeplitz(t, rows: int, cols: int | None = None) -> Op:
     if len(keep) != rows + cols - 1:
         raise ValueError("t must hold rows + cols - 1 entries")
     return Op(_lib.fm_toeplitz(p, rows, cols, dt, _stream()), kind="toeplitz")
+
+
+def toeplitz2(t, r1: int, c1: int, r2: int, c2: int) -> Op:
+    """Two-level Toeplitz matrix (r1 r2) x (c1 c2) from the row-major (r1 + c1 - 1) x (r2 + c2 - 1)
+    generator t (``fm_toeplitz2``)."""
+    if isinstance(t, torch.Tensor):
+        t = t.reshape(-1)
+    else:
+        t = np.asarray(t).reshape(-1)
+    p, dt, keep = _param(t)
+    if len(keep) != (r1 + c1 - 1) * (r2 + c2 - 1):
+        raise ValueError("t must hold (r1 + c1 - 1) (r2 + c2 - 1) entries")
+    return Op(_lib.fm_toeplitz2(p, r1, c1, r2, c2, dt, _stream()), kind="toeplitz2")
+
+
+def blocks(grid) -> Op:
+    """Block matrix of operators from a list of block rows (``fm_blocks``)."""
+    nr, nc = len(grid), len(grid[0])
+    if any(len(r) != nc for r in grid):
+        raise ValueError("every block row needs the same number of blocks")
+    flat = [b for r in grid for b in r]
+    return Op(_lib.fm_blocks([b.handle for b in flat], nr, nc), flat)
 
 
 def hadamard(log2n: int, mode: int = FM_HAD_FP32) -> Op:

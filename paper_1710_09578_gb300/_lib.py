@@ -69,6 +69,8 @@ _SIGS = {
     "fm_blkdiag": [_opp, _i32, _opp],
     "fm_kron": [_opp, _i32, _opp],
     "fm_hermitian": [_op, _opp],
+    "fm_blocks": [_opp, _i32, _i32, _opp],
+    "fm_toeplitz2": [_p, _i64, _i64, _i64, _i64, _i32, _p, _opp],
     "fm_shape": [_op, ctypes.POINTER(_i64), ctypes.POINTER(_i64)],
     "fm_is_real": [_op, ctypes.POINTER(_i32)],
     "fm_out_dtype": [_op, _i32, ctypes.POINTER(_i32)],
@@ -161,6 +163,14 @@ def fm_blkdiag(handles):
 
 def fm_kron(handles):
     return _new("fm_kron", _arr(handles), len(handles))
+
+
+def fm_blocks(handles, nrows: int, ncols: int):
+    return _new("fm_blocks", _arr(handles), nrows, ncols)
+
+
+def fm_toeplitz2(t_ptr: int, r1: int, c1: int, r2: int, c2: int, dt: int, stream: int = 0):
+    return _new("fm_toeplitz2", t_ptr, r1, c1, r2, c2, dt, stream)
 
 
 def fm_hermitian(h):

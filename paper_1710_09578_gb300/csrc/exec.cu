@@ -77,6 +77,7 @@ fm_status natural_out_dtype(const fm_op_s* A, fm_dtype in, fm_dtype* out) {
       return FM_OK;
     }
     case K_SUM:
+    case K_BLOCKS:
     case K_BLKDIAG: {
       fm_dtype r = in;
       bool first = true;
@@ -825,6 +826,27 @@ fm_status exec(const fm_op_s* A, bool adj, const View& in, const View& out, int6
     }
     case K_KRON:
       return exec_kron(A, adj, in, out, ncols, beta, ctx);
+    case K_BLOCKS: {
+      // output segment i = sum_j B_ij (input segment j); adjoint: segment j = sum_i B_ij^H (segment i)
+      const int R = A->blk_r, Cn = A->blk_c;
+      const int no = adj ? Cn : R, ni = adj ? R : Cn;
+      int64_t ooff = 0;
+      for (int a = 0; a < no; ++a) {
+        int64_t ioff = 0;
+        for (int b = 0; b < ni; ++b) {
+          const fm_op_s* B = adj ? A->kids[b * Cn + a] : A->kids[a * Cn + b];
+          View ii = in, oo = out;
+          ii.n = in_len(B, adj);
+          oo.n = out_len(B, adj);
+          ii.p = elem_ptr(in.p, in.dt, ioff * in.inner);
+          oo.p = elem_ptr(out.p, out.dt, ooff * out.inner);
+          FM_TRY(exec(B, adj, ii, oo, ncols, b == 0 ? beta : 1, ctx));
+          ioff += ii.n;
+        }
+        ooff += out_len(adj ? A->kids[a] : A->kids[a * Cn], adj);
+      }
+      return FM_OK;
+    }
   }
   set_error("unknown operator kind");
   return FM_ERR_INVALID_ARG;

@@ -131,7 +131,7 @@ fm_status noalloc_prepare(int device);
 // ------------------------------------------------------------------ operators
 enum OpKind {
   K_FOURIER, K_CIRCULANT, K_TOEPLITZ, K_HADAMARD, K_DIAG, K_PARTIAL,
-  K_PRODUCT, K_SUM, K_BLKDIAG, K_KRON, K_HERMITIAN
+  K_PRODUCT, K_SUM, K_BLKDIAG, K_KRON, K_HERMITIAN, K_BLOCKS
 };
 
 // Twiddles and spectra for a length-L transform done in two passes (L = N1 * N2): every
@@ -182,8 +182,9 @@ struct fm_op_s {
   std::vector<int32_t> idx_host;
   // two-pass plan for long transforms
   fm::BigPlan big;
-  // composites
+  // composites (Blocks: kids[i * blk_c + j] is block (i, j) of a blk_r x blk_c grid)
   std::vector<fm_op_s*> kids;
+  int blk_r = 0, blk_c = 0;
   fm::Workspace ws;
 };
 

@@ -479,6 +479,60 @@ def test_planted_param_grad_mistakes_are_caught():
     assert not np.allclose(bad, g["grad_t"])
 
 
+# ----------------------------------------------------------------- Blocks and two-level Toeplitz
+def test_golden_toeplitz2():
+    g = _kv("toeplitz2_2x2.txt")
+    T2 = O.Toeplitz2(g["t"].reshape(3, 3), 2, 2, 2, 2)
+    assert np.array_equal(T2.dense(), g["T"].reshape(4, 4))
+    assert np.allclose(T2.apply(g["x"]), g["y"])
+
+
+@pytest.mark.parametrize("r1,c1,r2,c2", [(3, 3, 4, 4), (2, 5, 3, 2), (15, 15, 15, 15), (1, 6, 7, 1)])
+def test_toeplitz2_separable_is_kron_of_toeplitz(r1, c1, r2, c2):
+    # a separable generator t[k1, k2] = a[k1] b[k2] makes T2 = T(a) (x) T(b) (scipy constructors)
+    a, b = crand(r1 + c1 - 1), crand(r2 + c2 - 1)
+    T2 = O.Toeplitz2(np.outer(a, b), r1, c1, r2, c2)
+
+    def sci(v, r, c):
+        return sla.toeplitz(v[:r], np.concatenate([v[:1], v[r:]]))
+
+    want = np.kron(sci(a, r1, c1), sci(b, r2, c2))
+    assert rel(T2.dense(), want) < 1e-14
+
+
+@pytest.mark.parametrize("r1,c1,r2,c2", [(3, 3, 4, 4), (2, 5, 3, 2), (9, 4, 5, 11)])
+def test_toeplitz2_fast_route_and_adjoint(r1, c1, r2, c2):
+    T2 = O.Toeplitz2(crand(r1 + c1 - 1, r2 + c2 - 1), r1, c1, r2, c2)
+    D = T2.dense()
+    X, Y = crand(c1 * c2, 3), crand(r1 * r2, 3)
+    assert rel(T2.apply(X), D @ X) < 1e-12
+    assert rel(T2.apply(Y, adjoint=True), D.conj().T @ Y) < 1e-12
+
+
+def test_blocks_dense_and_apply():
+    grid = [[O.Toeplitz(crand(5), 3, 3), O.Toeplitz(crand(4), 3, 2)],
+            [O.Toeplitz(crand(4), 2, 3), O.Fourier(2)]]
+    B = O.Blocks(grid)
+    want = np.block([[grid[0][0].dense(), grid[0][1].dense()], [grid[1][0].dense(), grid[1][1].dense()]])
+    assert rel(B.dense(), want) < 1e-15
+    X, Y = crand(5, 2), crand(5, 2)
+    assert rel(B.apply(X), want @ X) < 1e-13
+    assert rel(B.apply(Y, adjoint=True), want.conj().T @ Y) < 1e-13
+
+
+def test_eq7_block_is_zero_padded_two_level_circulant():
+    # Eq. (7): a two-level Toeplitz block is the row/column selection of
+    # (F (x) F)^H Diag(h) (F (x) F), with h the 2-D DFT of the embedded generator over L1 L2
+    r1, c1, r2, c2 = 3, 4, 2, 5
+    T2 = O.Toeplitz2(crand(r1 + c1 - 1, r2 + c2 - 1), r1, c1, r2, c2)
+    L1, L2 = T2.L1, T2.L2
+    FK = O.Kron(O.Fourier(L1), O.Fourier(L2))
+    C2 = FK.dense().conj().T @ np.diag(T2.spectrum.reshape(-1) / (L1 * L2)) @ FK.dense()
+    rows = [i1 * L2 + i2 for i1 in range(r1) for i2 in range(r2)]
+    cols = [j1 * L2 + j2 for j1 in range(c1) for j2 in range(c2)]
+    assert rel(C2[np.ix_(rows, cols)], T2.dense()) < 1e-12
+
+
 # ----------------------------------------------------------------- planted mistakes
 class _CirculantNoConj(O.Circulant):
     def _apply(self, X, adjoint):                       # forgets the conjugate in the adjoint
