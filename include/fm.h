@@ -90,6 +90,15 @@ fm_status fm_circulant(const void* c, int64_t n, fm_dtype dt, void* stream, fm_o
 fm_status fm_toeplitz(const void* t, int64_t rows, int64_t cols, fm_dtype dt, void* stream,
                       fm_op* out);
 
+/* Circulant whose first column is a pseudo-random +-1 sequence from a linear feedback shift
+ * register (the LFSRCirculant of Sec. 4; the paper gives no register conventions, so:) a
+ * Fibonacci register of nbits bits (1..63) starting from a nonzero `state`; each step outputs
+ * o = s & 1, forms f = parity(s & taps) and shifts s <- (s >> 1) | (f << (nbits - 1)); the column
+ * holds c[k] = +1 for o_k = 0 and -1 for o_k = 1, for the first n outputs (n a power of two,
+ * <= 2^24; a maximal-length sequence has period 2^nbits - 1).  The taps of x^m + x^a + 1 are
+ * bits 0 and a.  A real circulant, as fm_circulant. */
+fm_status fm_lfsr_circulant(int32_t nbits, uint64_t taps, uint64_t state, int64_t n, void* stream, fm_op* out);
+
 /* Sylvester Hadamard matrix H[i, j] = (-1)^popcount(i & j), natural order,
  * unnormalised, n = 2^log2n, 0 <= log2n <= 24 (BF16 modes: 4 <= log2n <= 16).
  * Symmetric, so forward and backward are the same map. */
@@ -220,6 +229,19 @@ fm_status fm_circulant_apply_noalloc(fm_op C, int adjoint, const void* X, int64_
 fm_status fm_param_grad(fm_op A, fm_op leaf, const void* X, int64_t ldx, fm_dtype xdt, const void* G, int64_t ldg,
                         fm_dtype gdt, int64_t ncols, void* grad, fm_dtype grad_dt, void* stream);
 
+/* Orthogonal matching pursuit (cited in Sec. 3 beside (F)ISTA; Sec. 4 names its rank-1 update
+ * form) for one right-hand side b (rows(A) entries) with K steps:
+ *   r_0 = b, S = [];  for k = 1..K: c = A^H r_{k-1}, j = argmax_i |c_i| (the lowest index among
+ *   equal magnitudes), S += [j], x_S = argmin ||A_S z - b||, r_k = b - A_S x_S;  x[S] = x_S.
+ * A enters only through fm_backward (correlations) and fm_forward (the column A e_j); the least
+ * squares solution is kept as a thin QR factorisation A_S = Q R extended by one column per step
+ * (classical Gram-Schmidt applied twice).  dt: C64 or C128 (any operator), or F32 / F64 for a
+ * real operator (solved in complex, real part returned).  b, x (cols(A) entries, overwritten)
+ * and support (K int32 picks in order, may be NULL) are DEVICE buffers.  1 <= K <= min(rows,
+ * cols, 4096).  Reductions run in a fixed order (bit-reproducible).  The call allocates its
+ * workspace (Q: K x rows) and synchronises `stream` before it returns. */
+fm_status fm_omp(fm_op A, const void* b, fm_dtype dt, int32_t K, void* x, int32_t* support, void* stream);
+
 /* ---------------------------------------------------------------- calibration */
 
 /* Calibration of the execution plan: the GPU form of the paper's calibration step
@@ -249,6 +271,21 @@ fm_status fm_calibrate(fm_op A, int64_t ncols, fm_dtype dt, void* stream, fm_tun
  * N1, L / N1 in [2^5, 2^13]; FM_OK if A has no transform of length L.  Same rules about
  * concurrent use as fm_calibrate. */
 fm_status fm_set_split(fm_op A, int64_t L, int64_t n1, void* stream);
+
+/* Dense execution of a small operator (Sec. 2.1.3: below some size a plain matrix-vector product
+ * beats the fast transform).  fm_set_dense(A, 1) materialises A's matrix once (the forward
+ * transform of the unit vectors, in FP64 and FP32) and from then on applies A to complex
+ * columns of plain blocks as y = M x (M^H y for the backward) from shared memory; real data and
+ * strided views keep the fast path, and A inside a Product is not fused with its neighbours.
+ * A: a Fourier, Circulant, Toeplitz or FP32 Hadamard operator with rows * cols <= 4096
+ * (FM_ERR_UNSUPPORTED otherwise).  fm_set_dense(A, 0) returns to the fast transform.
+ * fm_calibrate_dense times A's forward + adjoint on ncols probe columns of dt (C64 or C128)
+ * both ways (20 repetitions each, after 3 untimed), keeps the faster and reports both times
+ * (milliseconds per forward + adjoint) and the choice (1 dense, 0 fast; any output may be NULL).
+ * Both calls allocate and synchronise `stream`; A must not be in use on another stream. */
+fm_status fm_set_dense(fm_op A, int dense, void* stream);
+fm_status fm_calibrate_dense(fm_op A, int64_t ncols, fm_dtype dt, void* stream, float* ms_fast, float* ms_dense,
+                             int32_t* chosen);
 
 /* ---------------------------------------------------------------- FISTA */
 

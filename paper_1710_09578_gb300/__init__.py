@@ -20,10 +20,11 @@ from . import _lib
 from ._lib import (FM_HAD_BF16, FM_HAD_BF16X2, FM_HAD_FP32, FM_HAD_INT8, FmError,  # noqa: F401
                    fm_fista_params, fm_fista_report)
 
-__all__ = ["Op", "fourier", "circulant", "toeplitz", "toeplitz2", "hadamard", "diag", "partial", "product",
+__all__ = ["Op", "fourier", "circulant", "lfsr_circulant", "toeplitz", "toeplitz2", "hadamard", "diag", "partial",
+           "product",
            "blocks",
            "sum_", "blkdiag", "kron", "FmApply", "apply", "param_grad", "FmParamApply", "apply_params",
-           "FistaBatch", "fista", "FmError",
+           "FistaBatch", "fista", "omp", "FmError",
            "FM_HAD_FP32", "FM_HAD_BF16", "FM_HAD_BF16X2", "FM_HAD_INT8", "launch_count"]
 
 _TORCH2FM = {torch.int8: _lib.FM_I8, torch.int32: _lib.FM_I32, torch.float32: _lib.FM_F32,
@@ -159,6 +160,16 @@ class Op:
             os.replace(tmp, cache)
         return res
 
+    def set_dense(self, dense: bool = True):
+        """Apply this small leaf as a dense matrix product (True) or as the fast transform."""
+        _lib.fm_set_dense(self._h, 1 if dense else 0, _stream())
+
+    def calibrate_dense(self, ncols: int, dtype: torch.dtype = torch.complex64):
+        """Time the fast transform against the dense product and keep the faster (the
+        paper's calibration); returns {"ms_fast", "ms_dense", "dense"}."""
+        a, b, c = _lib.fm_calibrate_dense(self._h, ncols, _TORCH2FM[dtype], _stream())
+        return {"ms_fast": a, "ms_dense": b, "dense": bool(c)}
+
     def set_split(self, L: int, n1: int):
         """Use the split N1 x (L / N1) for every two-pass transform of length L (0: default)."""
         _lib.fm_set_split(self._h, L, n1, _stream())
@@ -188,6 +199,11 @@ def toeplitz(t, rows: int, cols: int | None = None) -> Op:
     if len(keep) != rows + cols - 1:
         raise ValueError("t must hold rows + cols - 1 entries")
     return Op(_lib.fm_toeplitz(p, rows, cols, dt, _stream()), kind="toeplitz")
+
+
+def lfsr_circulant(nbits: int, taps: int, state: int, n: int) -> Op:
+    """Circulant on the +-1 output of a Fibonacci LFSR (``fm_lfsr_circulant``)."""
+    return Op(_lib.fm_lfsr_circulant(nbits, taps, state, n, _stream()), kind="circulant")
 
 
 def toeplitz2(t, r1: int, c1: int, r2: int, c2: int) -> Op:
@@ -327,6 +343,18 @@ class FmParamApply(torch.autograd.Function):
 def apply_params(build, X: torch.Tensor, *params: torch.Tensor) -> torch.Tensor:
     """Differentiable A(params) X: see FmParamApply."""
     return FmParamApply.apply(X, build, *params)
+
+
+# ---------------------------------------------------------------- OMP
+def omp(A: Op, b: torch.Tensor, K: int):
+    """Orthogonal matching pursuit with K steps (``fm_omp``): returns (x, support)."""
+    if not b.is_cuda or b.dim() != 1 or b.numel() != A.rows:
+        raise ValueError("b must be a CUDA vector of rows(A) entries")
+    b = b.contiguous()
+    x = torch.empty(A.cols, dtype=b.dtype, device=b.device)
+    S = torch.empty(K, dtype=torch.int32, device=b.device)
+    _lib.fm_omp(A.handle, b.data_ptr(), _TORCH2FM[b.dtype], K, x.data_ptr(), S.data_ptr(), _stream())
+    return x, S
 
 
 # ---------------------------------------------------------------- FISTA

@@ -86,6 +86,11 @@ _SIGS = {
     "fm_calibrate": [_op, _i64, _i32, _p, ctypes.POINTER(fm_tune_entry), _i32, ctypes.POINTER(_i32)],
     "fm_set_split": [_op, _i64, _i64, _p],
     "fm_param_grad": [_op, _op, _p, _i64, _i32, _p, _i64, _i32, _i64, _p, _i32, _p],
+    "fm_omp": [_op, _p, _i32, _i32, _p, _p, _p],
+    "fm_lfsr_circulant": [_i32, ctypes.c_uint64, ctypes.c_uint64, _i64, _p, _opp],
+    "fm_set_dense": [_op, _i32, _p],
+    "fm_calibrate_dense": [_op, _i64, _i32, _p, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                           ctypes.POINTER(_i32)],
     "fm_trace_begin": [_i32],
     "fm_trace_end": [ctypes.POINTER(fm_trace_entry), _i32, ctypes.POINTER(_i32)],
 }
@@ -261,6 +266,26 @@ def fm_fista_batch(b, b_ptr: int, x_ptr: int, y_ptr: int | None, params: fm_fist
 def fm_param_grad(h, leaf, X: int, ldx: int, xdt: int, G: int, ldg: int, gdt: int, ncols: int, grad: int,
                   grad_dt: int, stream: int = 0):
     check(lib.fm_param_grad(h, leaf, X, ldx, xdt, G, ldg, gdt, ncols, grad, grad_dt, stream), "fm_param_grad")
+
+
+def fm_lfsr_circulant(nbits: int, taps: int, state: int, n: int, stream: int = 0):
+    return _new("fm_lfsr_circulant", nbits, taps, state, n, stream)
+
+
+def fm_set_dense(h, dense: int, stream: int = 0):
+    check(lib.fm_set_dense(h, dense, stream), "fm_set_dense")
+
+
+def fm_calibrate_dense(h, ncols: int, dt: int, stream: int = 0):
+    """Time forward + adjoint fast and dense; returns (ms_fast, ms_dense, chosen)."""
+    a, b, c = ctypes.c_float(), ctypes.c_float(), _i32()
+    check(lib.fm_calibrate_dense(h, ncols, dt, stream, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+          "fm_calibrate_dense")
+    return a.value, b.value, c.value
+
+
+def fm_omp(h, b: int, dt: int, K: int, x: int, support: int | None, stream: int = 0):
+    check(lib.fm_omp(h, b, dt, K, x, support, stream), "fm_omp")
 
 
 def fm_trace_begin(max_launches: int):

@@ -54,8 +54,8 @@ DeviceTables* device_tables_if_ready(int device) {
 void op_retain(fm_op_s* A) { A->refs.fetch_add(1); }
 
 static void free_op(fm_op_s* A) {
-  void* bufs[] = {A->spec64, A->spec32, A->spec64_perm, A->spec32_perm, A->d64, A->d32,
-                  A->dr64,   A->dr32,   A->idx,         A->inv,         A->ws.ptr};
+  void* bufs[] = {A->spec64, A->spec32, A->spec64_perm, A->spec32_perm, A->d64, A->d32, A->dr64,
+                  A->dr32,   A->idx,    A->inv,         A->ws.ptr,      A->m32, A->m64};
   for (void* p : bufs)
     if (p) cudaFree(p);
   free_big_plan(&A->big);

@@ -29,7 +29,7 @@ static fm_dtype promote(fm_dtype a, fm_dtype b) {
 }
 
 static bool is_fft_leaf(const fm_op_s* A) {
-  return (A->kind == K_FOURIER || A->kind == K_CIRCULANT || A->kind == K_TOEPLITZ) && A->L > 1;
+  return (A->kind == K_FOURIER || A->kind == K_CIRCULANT || A->kind == K_TOEPLITZ) && A->L > 1 && !A->dense;
 }
 
 fm_status natural_out_dtype(const fm_op_s* A, fm_dtype in, fm_dtype* out) {
@@ -789,6 +789,11 @@ fm_status exec(const fm_op_s* A, bool adj, const View& in, const View& out, int6
     FM_TRY(copy_view(t, out, ncols, beta, ctx));
     ctx.used = mark;
     return FM_OK;
+  }
+  if (A->dense && is_complex(in.dt) && in.dt == out.dt && in.outer == 1 && in.inner == 1 && out.outer == 1 &&
+      out.inner == 1) {
+    if (ctx.dry) return FM_OK;
+    return dense_apply(A, adj, in.p, in.ld, out.p, out.ld, ncols, is_double(in.dt), beta, ctx.st);
   }
   switch (A->kind) {
     case K_FOURIER:

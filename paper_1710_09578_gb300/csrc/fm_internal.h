@@ -124,6 +124,11 @@ fm_status device_tables(int device, DeviceTables** out);
 // The tables of `device` if they exist already, else nullptr (never allocates).
 DeviceTables* device_tables_if_ready(int device);
 
+// Dense product y = M x (adj: M^H x) of a leaf with fm_set_dense on, complex columns of one
+// precision (dense.cu).
+fm_status dense_apply(const fm_op_s* A, bool adj, const void* in, int64_t ldi, void* out, int64_t ldo,
+                      int64_t ncols, bool dbl, int beta, cudaStream_t st);
+
 // Look up (and so reserve) the static scratch of fm_circulant_apply_noalloc on `device`, the
 // current device; called when a Circulant operator is built there (noalloc.cu).
 fm_status noalloc_prepare(int device);
@@ -182,6 +187,10 @@ struct fm_op_s {
   std::vector<int32_t> idx_host;
   // two-pass plan for long transforms
   fm::BigPlan big;
+  // dense execution of a small leaf (fm_set_dense): the matrix, column-major rows x cols
+  int dense = 0;
+  float2* m32 = nullptr;
+  double2* m64 = nullptr;
   // composites (Blocks: kids[i * blk_c + j] is block (i, j) of a blk_r x blk_c grid)
   std::vector<fm_op_s*> kids;
   int blk_r = 0, blk_c = 0;

@@ -15,6 +15,8 @@ import scipy.linalg as sla
 
 import oracle as O
 import oracle.gradients as OG
+import oracle.omp as OMP
+import oracle.lfsr as OL
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 RNG = np.random.default_rng(1234)
@@ -531,6 +533,92 @@ def test_eq7_block_is_zero_padded_two_level_circulant():
     rows = [i1 * L2 + i2 for i1 in range(r1) for i2 in range(r2)]
     cols = [j1 * L2 + j2 for j1 in range(c1) for j2 in range(c2)]
     assert rel(C2[np.ix_(rows, cols)], T2.dense()) < 1e-12
+
+
+# ----------------------------------------------------------------- OMP
+class _DenseOp(O.Op):
+    def __init__(self, M):
+        self.M = np.asarray(M)
+        self.rows, self.cols = self.M.shape
+        self.real = self.M.dtype.kind != "c"
+
+    def dense(self):
+        return self.M
+
+    def _apply(self, X, adjoint):
+        return (self.M.conj().T if adjoint else self.M) @ X
+
+
+def test_golden_omp_with_tie():
+    g = _kv("omp2x3.txt")
+    A = _DenseOp(g["A"].reshape(2, 3))
+    x, S, res = OMP.omp(A, g["b"], 2, return_residuals=True)
+    assert S == [int(v) for v in g["S"]]
+    assert np.allclose(x, g["x"]) and np.allclose(res, g["res"], atol=1e-12)
+
+
+def test_omp_orthonormal_exact_recovery_and_order():
+    # A = F / sqrt(n) is unitary: A^H b = x0, so OMP picks the support in order of decreasing
+    # |x0| and recovers x0 exactly after K steps
+    n, K = 64, 6
+    A = O.Product(O.Diag(np.full(n, 1 / np.sqrt(n))), O.Fourier(n))
+    x0 = np.zeros(n, dtype=complex)
+    supp = RNG.choice(n, K, replace=False)
+    x0[supp] = np.exp(2j * np.pi * RNG.random(K)) * (2.0 ** -np.arange(K))
+    x, S = OMP.omp(A, A.apply(x0), K)
+    assert S == [int(j) for j in supp]
+    assert rel(x, x0) < 1e-12
+
+
+def test_omp_residual_orthogonal_to_selected_columns():
+    n = 32
+    A = O.Product(O.Partial(np.sort(RNG.choice(n, 20, replace=False)), n), O.Toeplitz(RNG.standard_normal(2 * n - 1), n, n))
+    b = RNG.standard_normal(20)
+    x, S, res = OMP.omp(A, b, 8, return_residuals=True)
+    r = b - A.apply(x)
+    AS = np.stack([OMP.column(A, j) for j in S], axis=1)
+    assert np.max(np.abs(AS.T @ r)) < 1e-10 * np.linalg.norm(b)
+    assert all(res[i + 1] <= res[i] + 1e-12 for i in range(len(res) - 1))
+    assert len(set(S)) == len(S)
+
+
+def _matching_pursuit(A, b, K):                          # no re-solve: only the new coefficient
+    r, x = b.astype(float).copy(), np.zeros(A.cols)
+    for _ in range(K):
+        c = A.apply(r, adjoint=True)
+        j = int(np.argmax(np.abs(c)))
+        a = OMP.column(A, j)
+        z = a @ r / (a @ a)
+        x[j] += z
+        r = r - z * a
+    return x
+
+
+def test_planted_omp_mistake_is_caught():
+    g = _kv("omp2x3.txt")
+    A = _DenseOp(g["A"].reshape(2, 3))
+    assert not np.allclose(_matching_pursuit(A, g["b"], 2), g["x"])
+
+
+# ----------------------------------------------------------------- LFSR circulant
+def test_golden_lfsr3():
+    g = _kv("lfsr3.txt")
+    assert np.array_equal(OL.lfsr_bits(3, 0b011, 0b001, 8), g["bits"].astype(np.int64))
+    C = OL.LFSRCirculant(3, 0b011, 0b001, 8)
+    assert np.array_equal(C.dense()[:, 0], g["c"])
+
+
+@pytest.mark.parametrize("m,a", [(5, 2), (7, 1), (10, 3)])
+def test_lfsr_maximal_length_properties(m, a):
+    # x^m + x^a + 1 primitive: period 2^m - 1, 2^(m-1) ones per period, two-level autocorrelation
+    P = (1 << m) - 1
+    bits = OL.lfsr_bits(m, 1 | (1 << a), 1, 2 * P)
+    assert np.array_equal(bits[:P], bits[P:])
+    assert all(not np.array_equal(bits[:P], np.roll(bits[:P], s)) for s in range(1, P))
+    assert bits[:P].sum() == 1 << (m - 1)
+    c = 1.0 - 2.0 * bits[:P]
+    ac = np.array([c @ np.roll(c, s) for s in range(P)])
+    assert ac[0] == P and np.all(ac[1:] == -1)
 
 
 # ----------------------------------------------------------------- planted mistakes
