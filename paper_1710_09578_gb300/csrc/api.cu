@@ -38,6 +38,9 @@ fm_status device_tables(int device, DeviceTables** out) {
     FM_CUDA(cudaMalloc(&t.tw32, sizeof(float2) * kTwMax));
     FM_CUDA(cudaMalloc(&t.tw64, sizeof(double2) * kTwMax));
     FM_TRY(twiddle_launch(kTwMax, t.tw32, t.tw64, nullptr));
+    FM_CUDA(cudaMalloc(&t.twp32, sizeof(float2) * kPassTwEntries));
+    FM_CUDA(cudaMalloc(&t.twp64, sizeof(double2) * kPassTwEntries));
+    FM_TRY(pass_twiddle_launch(t.twp32, t.twp64, nullptr));
     FM_CUDA(cudaStreamSynchronize(nullptr));
     g_tab_ready[device] = true;
   }

@@ -166,10 +166,11 @@ struct Fused {
   const fm_op_s* post_map = nullptr;  // Partial applied forward (gather) after the transform
 };
 
+// the pass-twiddle tables the tile passes read (fm_device.cuh)
 template <typename T>
 static const typename Cx<T>::t* tw_table(Ctx& ctx) {
-  if constexpr (sizeof(T) == 4) return ctx.tabs->tw32;
-  else return ctx.tabs->tw64;
+  if constexpr (sizeof(T) == 4) return ctx.tabs->twp32;
+  else return ctx.tabs->twp64;
 }
 
 template <typename T>

@@ -30,7 +30,7 @@ struct FftArgs {
   const C* spec = nullptr;  // length L (times spec_omod rows for per-row spectra)
   int64_t spec_omod = 1;    // spectrum row = o % spec_omod
   int spec_conj = 0;
-  const C* tw = nullptr;    // W_{kTwMax}^m table
+  const C* tw = nullptr;    // pass-twiddle tables (pass_tw_offset)
   // geometry
   int64_t ncu = 0, ncols = 0, outer = 1, inner = 1;
   int V = 1, logV = 0;

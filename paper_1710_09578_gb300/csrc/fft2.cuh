@@ -173,17 +173,57 @@ __device__ __forceinline__ void twiddle_powers(C* x, C w) {
   }
 }
 
+// The R twiddles W_{Ns R}^((j mod Ns) k), k < R, of butterfly j: one row of the pass-twiddle
+// table (fm_device.cuh), read as 16-byte vectors through the read-only path (the table is
+// written once per device, long before any transform).
+template <int LR>
+__device__ __forceinline__ void tw_row(float2 (&w)[1 << LR], const float2* row) {
+  constexpr int R = 1 << LR;
+#pragma unroll
+  for (int q = 0; q < R / 2; ++q) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(row) + q);
+    w[2 * q] = make_float2(v.x, v.y);
+    w[2 * q + 1] = make_float2(v.z, v.w);
+  }
+}
+template <int LR>
+__device__ __forceinline__ void tw_row(double2 (&w)[1 << LR], const double2* row) {
+#pragma unroll
+  for (int k = 0; k < (1 << LR); ++k) w[k] = __ldg(row + k);
+}
+
+// x * conj(w)
+template <typename C> __device__ __forceinline__ C cmul_conj(C a, C b) {
+  return cmake(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+
 template <typename C, bool VF, int THREADS, int EPT, int LOGL, int LOGV, int LR, int LOGNS>
-__device__ __forceinline__ void p2_compute(C (&r)[EPT], int dir, const C* __restrict__ tw) {
+__device__ __forceinline__ void p2_compute(C (&r)[EPT], int dir, const C* __restrict__ twp) {
   constexpr int R = 1 << LR;
 #pragma unroll
   for (int q = 0; q < EPT / R; ++q) {
     if (LOGNS > 0) {
       int j, v;
       bfly2<VF, THREADS, LOGL, LOGV, LR>(q, j, v);
-      C w = gld(tw + ((j & ((1 << LOGNS) - 1)) << (kTwLog - LOGNS - LR)));
-      if (dir > 0) w = cconj(w);
-      twiddle_powers<C, R>(&r[q * R], w);
+      const C* row = twp + pass_tw_offset(LOGNS + LR, LR) + ((int64_t)(j & ((1 << LOGNS) - 1)) << LR);
+      if constexpr (sizeof(C) == 16) {
+        // FP64: every power from the table (a product tree of FP64 multiplies costs more)
+        C w[R];
+        tw_row<LR>(w, row);
+        if (dir > 0) {
+#pragma unroll
+          for (int k = 1; k < R; ++k) r[q * R + k] = cmul_conj(r[q * R + k], w[k]);
+        } else {
+#pragma unroll
+          for (int k = 1; k < R; ++k) r[q * R + k] = cmul(r[q * R + k], w[k]);
+        }
+      } else {
+        // FP32: the base twiddle from the table and its powers by a product tree (measured
+        // faster on GB300 than reading all R - 1 powers: fewer loads in flight per butterfly)
+        C w = __ldg(row + 1);
+        if (dir > 0) w = cconj(w);
+        twiddle_powers<C, R>(&r[q * R], w);
+      }
     }
     if (R == 16) dft16(&r[q * R], dir);
     else if (R == 8) dft8(&r[q * R], dir);
@@ -192,7 +232,9 @@ __device__ __forceinline__ void p2_compute(C (&r)[EPT], int dir, const C* __rest
   }
 }
 
-template <typename C, bool VF, int THREADS, int EPT, int LOGL, int LOGV, int P, bool INV>
+// FRESH: the first pass's inputs came from global memory, so no thread can still be reading the
+// exchange buffer when the first pass writes it (the barrier before that write is skipped).
+template <typename C, bool VF, int THREADS, int EPT, int LOGL, int LOGV, int P, bool INV, bool FRESH = false>
 __device__ __forceinline__ void p2_run(C (&r)[EPT], C* s, int dir, const C* tw) {
   using S = Sched<LOGL, ept_lmax<EPT>()>;
   if constexpr (P < S::NR) {
@@ -201,11 +243,11 @@ __device__ __forceinline__ void p2_run(C (&r)[EPT], C* s, int dir, const C* tw) 
     if constexpr (P > 0) p2_read<C, VF, THREADS, EPT, LOGL, LOGV, LR>(r, s);
     p2_compute<C, VF, THREADS, EPT, LOGL, LOGV, LR, LOGNS>(r, dir, tw);
     if constexpr (P + 1 < S::NR) {
-      __syncthreads();
+      if constexpr (!(FRESH && P == 0)) __syncthreads();
       p2_write<C, VF, THREADS, EPT, LOGL, LOGV, LR, LOGNS>(r, s);
       __syncthreads();
     }
-    p2_run<C, VF, THREADS, EPT, LOGL, LOGV, P + 1, INV>(r, s, dir, tw);
+    p2_run<C, VF, THREADS, EPT, LOGL, LOGV, P + 1, INV, FRESH>(r, s, dir, tw);
   }
 }
 
@@ -379,7 +421,7 @@ __global__ void __launch_bounds__(THREADS, fft2_min_blocks<T, LOGL, THREADS, EPT
   constexpr int LRL = S::lr(S::NR - 1);
   C r[EPT];
   load_first<T, VF, SIMPLE, THREADS, EPT, LOGL, LOGV, LR0>(r, a, vinfo);
-  p2_run<C, VF, THREADS, EPT, LOGL, LOGV, 0, false>(r, s, a.dir0, a.tw);
+  p2_run<C, VF, THREADS, EPT, LOGL, LOGV, 0, false, true>(r, s, a.dir0, a.tw);
   if constexpr (CONV) {
     // spectrum product at the natural positions t = j + k L/R of the last forward radix
     constexpr int R = 1 << LRL;
@@ -390,7 +432,8 @@ __global__ void __launch_bounds__(THREADS, fft2_min_blocks<T, LOGL, THREADS, EPT
       const C* sp = a.spec + vinfo[v].soff + j;
 #pragma unroll
       for (int k = 0; k < R; ++k) {
-        C w = gld(sp + (k << (LOGL - LRL)));
+        // the spectrum is written once at construction: read-only path
+        C w = __ldg(sp + (k << (LOGL - LRL)));
         r[q * R + k] = cmul(r[q * R + k], a.spec_conj ? cconj(w) : w);
       }
     }

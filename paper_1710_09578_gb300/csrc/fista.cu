@@ -57,7 +57,7 @@ struct FistaArgs {
   float* const* xp;
   float* y;                // FISTA momentum state y_{k+1}, packed like x
   float* pw;               // power-iteration iterate, packed like x (may equal y)
-  const float2* tw;        // W_{2^14}^m, FFT passes
+  const float2* tw;        // pass-twiddle tables of the FFT passes
   const float2* tw2;       // W_{2^15}^m, real-FFT pre/post steps
   int iters, power_iters;
   double lambda_rel, safety;
@@ -692,7 +692,7 @@ static fm_status fista_run(fm_batch B, const float* b, float* x, const float* co
   a.xp = xp;
   a.y = y ? y : B->y;
   a.pw = B->y;
-  a.tw = tabs->tw32;
+  a.tw = tabs->twp32;
   a.tw2 = B->tw2;
   a.iters = p->iters;
   a.power_iters = p->power_iters;

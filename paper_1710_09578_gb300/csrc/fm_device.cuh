@@ -166,6 +166,17 @@ __device__ __forceinline__ void gst(double2* p, double2 v) {
   asm volatile("st.global.v2.f64 [%0], {%1, %2};" ::"l"(p), "d"(v.x), "d"(v.y) : "memory");
 }
 
+// Pass-twiddle tables: for a radix-2^lr pass of a Stockham transform whose butterflies span
+// 2^s = Ns * R elements, row i < Ns holds W_{2^s}^(i k), k = 0 .. R - 1 (W = exp(-2 pi i / 2^s)),
+// so a butterfly j reads row j mod Ns as R contiguous entries.  One block of 2^s entries per
+// (s, lr), s = 1 .. 14, lr = 1 .. min(4, s), in that order.
+__host__ __device__ constexpr int64_t pass_tw_offset(int s, int lr) {
+  int64_t off = 0;
+  for (int q = 1; q < s; ++q) off += (int64_t)(q < 4 ? q : 4) << q;
+  return off + ((int64_t)(lr - 1) << s);
+}
+constexpr int64_t kPassTwEntries = pass_tw_offset(15, 1);
+
 // Shared-memory index with one pad slot every 16 elements (breaks power-of-two strides).
 __device__ __forceinline__ int spad(int lin) { return lin + (lin >> 4); }
 

@@ -119,6 +119,8 @@ constexpr int kTwMax = 1 << kTwLog;
 struct DeviceTables {
   float2* tw32 = nullptr;
   double2* tw64 = nullptr;
+  float2* twp32 = nullptr;   // pass-twiddle tables of the Stockham passes (fm_device.cuh)
+  double2* twp64 = nullptr;
 };
 fm_status device_tables(int device, DeviceTables** out);
 // The tables of `device` if they exist already, else nullptr (never allocates).

@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(1 << (LA + LB - 4), 1) kron_hf_kernel(const __
       for (int k = 0; k < R; ++k) r[q * R + k] = gld(p + k * M);
     }
   }
-  p2_run<float2, false, THREADS, EPT, LB, LA, 0, false>(r, s, a.dir, a.tw);
+  p2_run<float2, false, THREADS, EPT, LB, LA, 0, false, true>(r, s, a.dir, a.tw);
   __syncthreads();
   p2_write<float2, false, THREADS, EPT, LB, LA, LRL, LB - LRL>(r, s);  // natural order, rows contiguous
   __syncthreads();

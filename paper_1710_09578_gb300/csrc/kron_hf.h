@@ -17,7 +17,7 @@ struct KronHFArgs {
   int dir = -1;                   // Fourier direction: -1 forward, +1 adjoint
   float scale = 1.f;              // 1, or 1/sqrt(2^LB) for the orthonormal Fourier matrix
   int beta = 0;                   // 1: accumulate into out
-  const float2* tw = nullptr;     // W_{2^14}^m table
+  const float2* tw = nullptr;     // pass-twiddle tables (pass_tw_offset)
 };
 
 // Tiles [2^la][2^lb] with 2^10 <= 2^(la+lb) <= 2^14 and 4 <= la, lb <= 8.

@@ -94,6 +94,30 @@ __global__ void twiddle_kernel(int64_t N, float2* t32, double2* t64) {
   }
 }
 
+// Entry q of the pass-twiddle tables (layout in fm_device.cuh), from sincospi in FP64.
+__global__ void pass_twiddle_kernel(float2* t32, double2* t64) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < kPassTwEntries;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    int s = 1, lr = 1;
+    while (q >= pass_tw_offset(s, lr) + ((int64_t)1 << s)) {
+      if (lr < (s < 4 ? s : 4)) ++lr;
+      else { ++s; lr = 1; }
+    }
+    const int64_t r = q - pass_tw_offset(s, lr);
+    const int64_t i = r >> lr, k = r & ((1 << lr) - 1);
+    const int64_t e = (i * k) & (((int64_t)1 << s) - 1);
+    double sn, cs;
+    sincospi(-2.0 * (double)e / (double)((int64_t)1 << s), &sn, &cs);
+    t64[q] = make_double2(cs, sn);
+    t32[q] = make_float2((float)cs, (float)sn);
+  }
+}
+
+fm_status pass_twiddle_launch(float2* t32, double2* t64, cudaStream_t st) {
+  pass_twiddle_kernel<<<256, 256, 0, st>>>(t32, t64);
+  return after_launch("pass_twiddle_kernel");
+}
+
 fm_status twiddle_launch(int64_t N, float2* t32, double2* t64, cudaStream_t st) {
   int64_t blocks = (N + 255) / 256;
   if (blocks > 4096) blocks = 4096;

@@ -31,6 +31,8 @@ fm_status pointwise_launch(const PwArgs& a, bool dbl, cudaStream_t st);
 fm_status i32_copy_launch(const int* in, int64_t in_ld, int* out, int64_t out_ld, int64_t n, int64_t ncols,
                           int beta, cudaStream_t st);
 fm_status twiddle_launch(int64_t N, float2* t32, double2* t64, cudaStream_t st);
+// the pass-twiddle tables of the Stockham passes (layout: pass_tw_offset in fm_device.cuh)
+fm_status pass_twiddle_launch(float2* t32, double2* t64, cudaStream_t st);
 fm_status spectrum_finish_launch(double2* s64, float2* s32, double2* p64, float2* p32, int64_t L, int64_t N1,
                                  int64_t N2, double scale, cudaStream_t st);
 fm_status to_c128_launch(const void* src, fm_dtype dt, int64_t n, int64_t dst_len, double2* dst, cudaStream_t st);
