@@ -372,6 +372,8 @@ def main():
     Y = torch.empty_like(X)
     Z = torch.empty_like(X)
     K.reserve(KRON_K, torch.complex64)
+    # set-up: the execution plan of the operator's transforms for this column count
+    kron_plan = [[e["L"], e["kind"], e["value"]] for e in K.calibrate(KRON_K, torch.complex64)]
 
     def step():
         K.forward(X, out=Y)
@@ -493,6 +495,8 @@ def main():
             "config": {"workload": WORKLOAD, "n": KRON_N, "columns": KRON_K, "bytes_per_step": STEP_BYTES,
                        "l2": "inputs larger than L2: each 512 MiB buffer is 4x the L2, steps back to back",
                        "streams": "one stream (the operator's workspace is per operator)",
+                       "plan": {"calibrated": kron_plan,
+                                "format": "[L, kind (0 split, 1 tile shape, 2 radix schedule), chosen value]"},
                        "parallelism": f"replicas x{world}"},
             "clocks": clk.summary(),
             "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": KRON_N * KRON_K * 8,
@@ -609,7 +613,7 @@ def measure_rows(fm, torch, dev, stream, l2, peak, peak_src, pool):
 
     rows["cs_PDC_2p18x64_fwd+adj"] = {
         "GB/s": g, "frac_of_hbm": g / peak, "algorithmic_bytes": byts,
-        "calibrated_split": [[e["L"], e["n1"]] for e in tune],
+        "calibrated_plan": [[e["L"], e["kind"], e["value"]] for e in tune],
         "kernels": trace_kernels(fm, cs_fn, 5, torch),
         "rel_err_vs_fp64": {"forward": e_f, "adjoint": e_b, "tolerance": 1e-5 * 18, "sample": "columns 0 and 63"},
         "cufft_reference_GB/s": _gbs_loop(torch_cs, byts, 20, flush, stream, torch),
@@ -624,7 +628,7 @@ def measure_rows(fm, torch, dev, stream, l2, peak, peak_src, pool):
     fb = 2 * 64 * n * 8
     g = _gbs_loop(lambda: F.forward(Xg, out=Yg), fb, 50, flush, stream, torch)
     rows["fourier_2p18x64_fwd"] = {
-        "GB/s": g, "frac_of_hbm": g / peak, "calibrated_split": [[e["L"], e["n1"]] for e in tuneF],
+        "GB/s": g, "frac_of_hbm": g / peak, "calibrated_plan": [[e["L"], e["kind"], e["value"]] for e in tuneF],
         "rel_err_vs_fp64": rel_err(Yg[cs_cols].cpu().numpy(), np.fft.fft(Xc[cs_cols].astype(np.complex128), axis=1)),
         "tolerance": 1e-5 * 18,
         "cufft_reference_GB/s": _gbs_loop(lambda: torch.fft.fft(Xg), fb, 50, flush, stream, torch)}
@@ -687,6 +691,7 @@ def profile_run(fm, torch, dev, which, steps):
         ck, Xk, _ = I.kron_large()
         A = fm.kron(fm.hadamard(8), fm.circulant(ck), fm.fourier(64))
         Xg = torch.from_numpy(Xk).to(dev)
+        A.calibrate(Xg.shape[0], torch.complex64)   # as in the bench step
         fn = lambda: A.backward(A.forward(Xg))  # noqa: E731
     elif which == "circulant_c128":
         c0, X0, _ = I.circulant_tiny()
@@ -743,7 +748,7 @@ def measure_fista(fm, torch, dev, stream, pool):
     b = torch.from_numpy(np.concatenate(bh)).to(dev)
     B = fm.FistaBatch(ops)
     x = torch.empty(B.total_cols, dtype=torch.float32, device=dev)
-    B.solve(b, x=x)                       # warm-up
+    order = B.tune(b, x=x)                # set-up: the work-list order (also the warm-up)
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g):
@@ -800,6 +805,8 @@ def measure_fista(fm, torch, dev, stream, pool):
     solves = FISTA_INSTANCES / t_batch
     return {"solves/s": solves, "ms_per_batch": t_batch * 1e3, "instances": FISTA_INSTANCES,
             "iterations": FISTA_ITERS, "graph": True,
+            "work_list_order": {"chosen": ["largest first", "smallest first"][order["order"]],
+                                "ms_largest_first": order["ms"][0], "ms_smallest_first": order["ms"][1]},
             "max_rel_err_vs_fp64": max(errs), "rel_err_sample": f"{len(sample)} instances, 2 per size, full groups",
             "tolerance": 1e-4,
             "operator_api_solves/s": ns / t_api, "operator_api_sample": ns,

@@ -245,24 +245,29 @@ fm_status fm_omp(fm_op A, const void* b, fm_dtype dt, int32_t K, void* x, int32_
 /* ---------------------------------------------------------------- calibration */
 
 /* Calibration of the execution plan: the GPU form of the paper's calibration step
- * (Sec. 2.1.3), which times an operator's transforms and keeps what it learns.  A
- * transform longer than one tile (Fourier, Circulant or Toeplitz embedding of length
- * L > 8192) runs as two passes over an N1 x N2 split of L; which split is fastest depends
- * on the operator (a convolution or a plain transform, the fused neighbours) and on the
- * number of columns.  fm_calibrate times A's forward + adjoint on ncols probe columns of
- * complex_of(dt) for each candidate split of each such transform in A (N1 = 2^e with both
- * N1 and N2 between 2^5 and 2^13), one transform at a time, and keeps the fastest in A.
- * Results are unchanged up to FP rounding.  It allocates and frees its probe buffers and
- * synchronises `stream`; A must not be in use on another stream meanwhile.
- * report (host, optional): one entry per tuned transform, at most max_entries; *n_entries
- * (optional) receives the number of tuned transforms.  A without such a transform: FM_OK,
- * *n_entries = 0. */
+ * (Sec. 2.1.3), which times an operator's transforms and keeps what it learns.  The settings
+ * it chooses, among variants compiled into the library:
+ *   kind 0  the split L = N1 x N2 of a transform longer than one tile (Fourier, Circulant or
+ *           Toeplitz embedding of length L > 8192), N1 = 2^e with N1, N2 in [2^5, 2^13];
+ *   kind 1  the tile shape of an FFT leaf's strided views: 0 automatic (wide tiles of 8 or 16
+ *           vectors for inner strides >= 16), 1 the default tile (2^12 elements), 2 the wide
+ *           tile wherever it applies (lengths 2^9 .. 2^10 in FP32, 2^9 in FP64);
+ *   kind 2  the radix schedule of an FFT leaf's tiles: 0 the per-length table (radix 16
+ *           first), 3 radices of at most 8 (compiled for FP32 tiles of 2^9 .. 2^12).
+ * fm_calibrate times A's forward + adjoint (one warm-up, mean of three) on ncols probe columns
+ * of complex_of(dt) for every candidate of every setting of every transform in A, one setting
+ * at a time (splits first, then per leaf the tile shape, then the radix schedule), and keeps
+ * the fastest in A.  Results are unchanged up to FP rounding.  It allocates and frees its probe
+ * buffers and synchronises `stream`; A must not be in use on another stream meanwhile.
+ * report (host, optional): one entry per tuned setting, at most max_entries; *n_entries
+ * (optional) receives the number of tuned settings (0 for an operator without FFT leaves). */
 typedef struct {
   int64_t L;            /* transform length */
-  int64_t n1;           /* chosen N1 (N2 = L / N1) */
+  int64_t n1;           /* chosen value (kind 0: N1, N2 = L / N1; kind 1: tile shape; kind 2: radix cap) */
   int32_t ncand;        /* candidates timed (<= 8) */
-  int64_t cand_n1[8];   /* their N1 */
-  float ms[8];          /* forward + adjoint of A with that split, milliseconds */
+  int64_t cand_n1[8];   /* their values */
+  float ms[8];          /* forward + adjoint of A with that value, milliseconds */
+  int32_t kind;         /* 0 split, 1 tile shape, 2 radix schedule */
 } fm_tune_entry;
 fm_status fm_calibrate(fm_op A, int64_t ncols, fm_dtype dt, void* stream, fm_tune_entry* report,
                        int32_t max_entries, int32_t* n_entries);
@@ -271,6 +276,13 @@ fm_status fm_calibrate(fm_op A, int64_t ncols, fm_dtype dt, void* stream, fm_tun
  * N1, L / N1 in [2^5, 2^13]; FM_OK if A has no transform of length L.  Same rules about
  * concurrent use as fm_calibrate. */
 fm_status fm_set_split(fm_op A, int64_t L, int64_t n1, void* stream);
+/* Set one plan setting (kind and value as in fm_tune_entry) of every FFT leaf of length L in A,
+ * e.g. to restore a cached calibration.  FM_ERR_INVALID_ARG for a value outside the kind's
+ * range; FM_OK if A has no leaf of length L. */
+fm_status fm_set_plan(fm_op A, int64_t L, int32_t kind, int64_t value, void* stream);
+/* A text description of A's tree (kinds, shapes, real or complex, Hadamard mode, Fourier
+ * scaling), for keying cached calibrations; FM_ERR_SHAPE if it needs more than len bytes. */
+fm_status fm_signature(fm_op A, char* buf, int32_t len);
 
 /* Dense execution of a small operator (Sec. 2.1.3: below some size a plain matrix-vector product
  * beats the fast transform).  fm_set_dense(A, 1) materialises A's matrix once (the forward
@@ -357,6 +369,17 @@ fm_status fm_batch_sizes(fm_batch B, int64_t* total_rows, int64_t* total_cols);
  * No allocation and no host synchronisation: capturable in a CUDA graph. */
 fm_status fm_fista_batch(fm_batch B, const float* b, float* x, float* y, const fm_fista_params* p,
                          const fm_fista_report* rep, void* stream);
+
+/* The persistent solve's work list as part of the calibration: each CTA takes the next group
+ * of equal-size instances, and the order of the groups decides how the last wave fills the
+ * GPU.  fm_batch_tune times one cold persistent solve (p->warm = 0, p->mode = 0, after one
+ * untimed) with the groups largest first (0, the default) and smallest first (1), keeps the
+ * faster for later solves of B, and reports the milliseconds (ms[2], host, may be NULL) and the
+ * choice (*chosen, may be NULL).  It writes x and synchronises `stream`. */
+fm_status fm_batch_tune(fm_batch B, const float* b, float* x, const fm_fista_params* p, void* stream, float* ms,
+                        int32_t* chosen);
+/* Set the work-list order (0 largest first, 1 smallest first), e.g. to restore a tuned choice. */
+fm_status fm_batch_set_order(fm_batch B, int32_t order);
 
 /* ---------------------------------------------------------------- tracing */
 

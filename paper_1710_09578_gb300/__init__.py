@@ -131,34 +131,45 @@ class Op:
         """Grow the workspace so that later calls on up to ncols columns allocate nothing."""
         _lib.fm_reserve(self._h, ncols, _TORCH2FM[dtype], _stream())
 
+    def signature(self) -> str:
+        """Text description of the operator tree (``fm_signature``)."""
+        return _lib.fm_signature(self._h)
+
     def calibrate(self, ncols: int, dtype: torch.dtype = torch.complex64, cache: str | None = None,
                   key: str | None = None):
-        """Pick the fastest two-pass split for every long transform in this operator by timing
-        forward + adjoint on ncols probe columns (the GPU form of the paper's calibration).
+        """Choose the execution plan of every transform in this operator by timing forward +
+        adjoint on ncols probe columns (the GPU form of the paper's calibration): the split of
+        long transforms, the tile shape of strided views and the radix schedule.
 
-        With `cache` (a JSON file path) the result is stored under `key` (default: shape,
-        ncols and dtype) and a later call with the same key restores it without timing.
-        Returns the list of {"L", "n1", "ms"} entries that were applied."""
+        With `cache` (a JSON file path) the choices are stored under `key` (default: the
+        operator's signature, ncols, dtype and the GPU's SM count) and a later call with the
+        same key restores them without timing.  Returns the list of {"L", "kind", "value", "ms"}
+        entries that were applied (kind 0 split, 1 tile shape, 2 radix schedule)."""
         import json
         import os
-        key = key or f"{self.shape[0]}x{self.shape[1]}:{ncols}:{str(dtype).replace('torch.', '')}"
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        key = key or f"{self.signature()}|n={self.cols}|ncols={ncols}|{str(dtype).replace('torch.', '')}|sm={sms}"
         table = {}
         if cache and os.path.exists(cache):
             with open(cache) as f:
                 table = json.load(f)
         if key in table:
             for e in table[key]:
-                _lib.fm_set_split(self._h, int(e["L"]), int(e["n1"]), _stream())
+                _lib.fm_set_plan(self._h, int(e["L"]), int(e["kind"]), int(e["value"]), _stream())
             return table[key]
         res = _lib.fm_calibrate(self._h, ncols, _TORCH2FM[dtype], _stream())
         if cache:
-            table[key] = [{"L": e["L"], "n1": e["n1"], "ms": {str(k): v for k, v in e["ms"].items()}}
-                          for e in res]
+            table[key] = [{"L": e["L"], "kind": e["kind"], "value": e["value"],
+                           "ms": {str(k): v for k, v in e["ms"].items()}} for e in res]
             tmp = cache + ".tmp"
             with open(tmp, "w") as f:
                 json.dump(table, f, indent=1, sort_keys=True)
             os.replace(tmp, cache)
         return res
+
+    def set_plan(self, L: int, kind: int, value: int):
+        """Set one execution-plan choice of every transform of length L (``fm_set_plan``)."""
+        _lib.fm_set_plan(self._h, L, kind, value, _stream())
 
     def set_dense(self, dense: bool = True):
         """Apply this small leaf as a dense matrix product (True) or as the fast transform."""
@@ -372,6 +383,20 @@ class FistaBatch:
         if b:
             _lib.fm_batch_release(b)
             self._b = None
+
+    def tune(self, b: torch.Tensor, x: torch.Tensor | None = None, iters: int = 200, power_iters: int = 20,
+             lambda_rel: float = 0.01, safety: float = 1.05, accel: bool = True):
+        """Choose the work-list order of the persistent solve by timing both (``fm_batch_tune``);
+        returns {"ms": [largest first, smallest first], "order": 0 or 1}."""
+        if x is None:
+            x = torch.empty(self.total_cols, dtype=torch.float32, device=b.device)
+        params = fm_fista_params(iters, power_iters, lambda_rel, safety, 1 if accel else 0, 0, 0, 0)
+        ms, c = _lib.fm_batch_tune(self._b, b.data_ptr(), x.data_ptr(), params, _stream())
+        return {"ms": ms, "order": c}
+
+    def set_order(self, order: int):
+        """Work-list order of the persistent solve: 0 largest instances first, 1 smallest first."""
+        _lib.fm_batch_set_order(self._b, order)
 
     def solve(self, b: torch.Tensor, x: torch.Tensor | None = None, iters: int = 200, power_iters: int = 20,
               lambda_rel: float = 0.01, safety: float = 1.05, accel: bool = True, mode: int = 0,

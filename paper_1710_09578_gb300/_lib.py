@@ -44,7 +44,7 @@ class fm_trace_entry(ctypes.Structure):
 
 class fm_tune_entry(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int64), ("n1", ctypes.c_int64), ("ncand", ctypes.c_int32),
-                ("cand_n1", ctypes.c_int64 * 8), ("ms", ctypes.c_float * 8)]
+                ("cand_n1", ctypes.c_int64 * 8), ("ms", ctypes.c_float * 8), ("kind", ctypes.c_int32)]
 
 
 if not os.path.exists(LIB_PATH):
@@ -83,8 +83,13 @@ _SIGS = {
     "fm_fista": [_opp, _i64, ctypes.POINTER(_p), ctypes.POINTER(_p), ctypes.POINTER(fm_fista_params),
                  ctypes.POINTER(fm_fista_report), _p],
     "fm_fista_batch": [_p, _p, _p, _p, ctypes.POINTER(fm_fista_params), ctypes.POINTER(fm_fista_report), _p],
+    "fm_batch_set_order": [_p, _i32],
+    "fm_batch_tune": [_p, _p, _p, ctypes.POINTER(fm_fista_params), _p, ctypes.POINTER(ctypes.c_float),
+                      ctypes.POINTER(_i32)],
     "fm_calibrate": [_op, _i64, _i32, _p, ctypes.POINTER(fm_tune_entry), _i32, ctypes.POINTER(_i32)],
     "fm_set_split": [_op, _i64, _i64, _p],
+    "fm_set_plan": [_op, _i64, _i32, _i64, _p],
+    "fm_signature": [_op, ctypes.c_char_p, _i32],
     "fm_param_grad": [_op, _op, _p, _i64, _i32, _p, _i64, _i32, _i64, _p, _i32, _p],
     "fm_omp": [_op, _p, _i32, _i32, _p, _p, _p],
     "fm_lfsr_circulant": [_i32, ctypes.c_uint64, ctypes.c_uint64, _i64, _p, _opp],
@@ -213,16 +218,26 @@ def fm_reserve(h, ncols: int, xdt: int, stream: int = 0):
 
 
 def fm_calibrate(h, ncols: int, dt: int, stream: int = 0):
-    """Time the candidate splits of every two-pass transform of h; returns one dict per
-    tuned transform: L, chosen n1, and {n1: ms} for the candidates."""
+    """Time the candidates of every plan setting of h; returns one dict per tuned setting:
+    L, kind (0 split, 1 tile shape, 2 radix schedule), the chosen value and {value: ms}."""
     rep = (fm_tune_entry * 64)()
     n = _i32(0)
     check(lib.fm_calibrate(h, ncols, dt, stream, rep, 64, ctypes.byref(n)), "fm_calibrate")
     out = []
     for e in rep[:min(n.value, 64)]:
-        out.append({"L": int(e.L), "n1": int(e.n1),
+        out.append({"L": int(e.L), "kind": int(e.kind), "value": int(e.n1),
                     "ms": {int(e.cand_n1[i]): float(e.ms[i]) for i in range(e.ncand)}})
     return out
+
+
+def fm_set_plan(h, L: int, kind: int, value: int, stream: int = 0):
+    check(lib.fm_set_plan(h, L, kind, value, stream), "fm_set_plan")
+
+
+def fm_signature(h) -> str:
+    buf = ctypes.create_string_buffer(1 << 16)
+    check(lib.fm_signature(h, buf, len(buf)), "fm_signature")
+    return buf.value.decode()
 
 
 def fm_set_split(h, L: int, n1: int, stream: int = 0):
@@ -255,6 +270,18 @@ def fm_fista(handles, b_ptrs, x_ptrs, params: fm_fista_params, report: fm_fista_
     xp = (ctypes.c_void_p * n)(*x_ptrs)
     rep = ctypes.byref(report) if report is not None else None
     check(lib.fm_fista(_arr(handles), n, bp, xp, ctypes.byref(params), rep, stream), "fm_fista")
+
+
+def fm_batch_set_order(b, order: int):
+    check(lib.fm_batch_set_order(b, order), "fm_batch_set_order")
+
+
+def fm_batch_tune(b, b_ptr: int, x_ptr: int, params: fm_fista_params, stream: int = 0):
+    """Time the two work-list orders; returns ([ms largest first, ms smallest first], chosen)."""
+    ms = (ctypes.c_float * 2)()
+    c = _i32()
+    check(lib.fm_batch_tune(b, b_ptr, x_ptr, ctypes.byref(params), stream, ms, ctypes.byref(c)), "fm_batch_tune")
+    return [float(ms[0]), float(ms[1])], int(c.value)
 
 
 def fm_fista_batch(b, b_ptr: int, x_ptr: int, y_ptr: int | None, params: fm_fista_params,

@@ -7,6 +7,8 @@
 // cheapest split depends on the operator and the column count.  The candidates are timed
 // on the operator as a whole (forward + adjoint, CUDA events) and the best one is kept.
 #include <algorithm>
+#include <cstring>
+#include <string>
 #include <vector>
 
 #include "fm_internal.h"
@@ -38,6 +40,33 @@ void collect(fm_op_s* A, std::vector<fm_op_s*>& out) {
     if (std::find(out.begin(), out.end(), A) == out.end()) out.push_back(A);
   }
   for (fm_op_s* k : A->kids) collect(k, out);
+}
+
+// Every FFT leaf (Fourier, Circulant, Toeplitz) whose tiles have a plan to choose.
+void collect_fft(fm_op_s* A, std::vector<fm_op_s*>& out) {
+  if (!A) return;
+  if ((A->kind == K_FOURIER || A->kind == K_CIRCULANT || A->kind == K_TOEPLITZ) && A->L > 1 && !A->dense) {
+    if (std::find(out.begin(), out.end(), A) == out.end()) out.push_back(A);
+  }
+  for (fm_op_s* k : A->kids) collect_fft(k, out);
+}
+
+void signature(const fm_op_s* A, std::string& out) {
+  static const char* names[] = {"F", "C", "T", "H", "D", "P", "Prod", "Sum", "BlkDiag", "Kron", "Herm", "Blocks"};
+  out += names[A->kind];
+  out += "[" + std::to_string(A->rows) + "x" + std::to_string(A->cols) + (A->real ? "r" : "c");
+  if (A->kind == K_HADAMARD) out += ",m" + std::to_string((int)A->had_mode);
+  if (A->kind == K_FOURIER && A->ortho) out += ",o";
+  if (A->kind == K_BLOCKS) out += "," + std::to_string(A->blk_r) + "x" + std::to_string(A->blk_c);
+  out += "]";
+  if (!A->kids.empty()) {
+    out += "(";
+    for (size_t i = 0; i < A->kids.size(); ++i) {
+      if (i) out += ",";
+      signature(A->kids[i], out);
+    }
+    out += ")";
+  }
 }
 
 bool split_ok(int64_t L, int64_t n1) {
@@ -85,15 +114,41 @@ fm_status fm_set_split(fm_op A, int64_t L, int64_t n1, void* stream) {
   return FM_OK;
 }
 
+fm_status fm_set_plan(fm_op A, int64_t L, int32_t kind, int64_t value, void* stream) {
+  clear_error();
+  if (!A) { set_error("null operator"); return FM_ERR_INVALID_ARG; }
+  if (kind == 0) return fm_set_split(A, L, value, stream);
+  if ((kind == 1 && (value < 0 || value > 2)) || (kind == 2 && value != 0 && value != 3) || kind < 0 || kind > 2) {
+    set_error("plan setting %d = %lld: tile shape 0..2, radix cap 0 or 3", kind, (long long)value);
+    return FM_ERR_INVALID_ARG;
+  }
+  std::vector<fm_op_s*> fl;
+  collect_fft(A, fl);
+  for (fm_op_s* leaf : fl)
+    if (leaf->L == L) (kind == 1 ? leaf->tile : leaf->rcap) = (int)value;
+  return FM_OK;
+}
+
+fm_status fm_signature(fm_op A, char* buf, int32_t len) {
+  clear_error();
+  if (!A || !buf || len < 1) { set_error("bad argument"); return FM_ERR_INVALID_ARG; }
+  std::string sgn;
+  signature(A, sgn);
+  if ((int64_t)sgn.size() + 1 > len) { set_error("signature needs %zu bytes", sgn.size() + 1); return FM_ERR_SHAPE; }
+  std::memcpy(buf, sgn.c_str(), sgn.size() + 1);
+  return FM_OK;
+}
+
 fm_status fm_calibrate(fm_op A, int64_t ncols, fm_dtype dt, void* stream, fm_tune_entry* report,
                        int32_t max_entries, int32_t* n_entries) {
   clear_error();
   if (n_entries) *n_entries = 0;
   if (!A || ncols <= 0) { set_error("bad argument"); return FM_ERR_INVALID_ARG; }
   if (dt != FM_F32 && dt != FM_F64 && dt != FM_C64 && dt != FM_C128) { set_error("calibration dtype"); return FM_ERR_DTYPE; }
-  std::vector<fm_op_s*> leaves;
+  std::vector<fm_op_s*> leaves, fleaves;
   collect(A, leaves);
-  if (leaves.empty()) return FM_OK;
+  collect_fft(A, fleaves);
+  if (leaves.empty() && fleaves.empty()) return FM_OK;
   cudaStream_t st = (cudaStream_t)stream;
   const fm_dtype cdt = complex_of(dt);
   const size_t esz = (size_t)dtype_size(cdt);
@@ -162,8 +217,42 @@ fm_status fm_calibrate(fm_op A, int64_t ncols, fm_dtype dt, void* stream, fm_tun
     if (s == FM_OK) s = s2;
     if (s != FM_OK) break;
     ent.n1 = best;
+    ent.kind = 0;
     if (report && done < max_entries) report[done] = ent;
     ++done;
+  }
+  // the plan of each FFT leaf's tiles: tile shape of strided views, then the radix cap
+  std::vector<fm_op_s*> fl;
+  collect_fft(A, fl);
+  for (fm_op_s* leaf : fl) {
+    if (s != FM_OK) break;
+    for (int kind = 1; kind <= 2 && s == FM_OK; ++kind) {
+      int* field = kind == 1 ? &leaf->tile : &leaf->rcap;
+      const std::vector<int> cand = kind == 1 ? std::vector<int>{0, 1, 2} : std::vector<int>{0, 3};
+      const int start = *field;
+      int best = start;
+      float best_ms = 0.f;
+      fm_tune_entry ent = {};
+      ent.L = leaf->L;
+      ent.kind = kind;
+      for (int c : cand) {
+        *field = c;
+        float ms = 0.f;
+        s = time_once(&ms);
+        if (s != FM_OK) break;
+        ent.cand_n1[ent.ncand] = c;
+        ent.ms[ent.ncand] = ms;
+        ent.ncand++;
+        if (best_ms == 0.f || ms < best_ms) {
+          best_ms = ms;
+          best = c;
+        }
+      }
+      *field = s == FM_OK ? best : start;
+      ent.n1 = *field;
+      if (report && done < max_entries) report[done] = ent;
+      ++done;
+    }
   }
   if (s == FM_OK) {
     cudaError_t e = cudaStreamSynchronize(st);

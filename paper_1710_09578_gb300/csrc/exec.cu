@@ -195,6 +195,7 @@ struct FftJob {
   double scale = 1.0;
   int64_t Lin = 0, Lout = 0;  // lengths of the transform's input and output vectors
   bool real = false;          // operator (with fused diagonals) is real
+  int tile = 0, rcap = 0;     // execution plan of the tiles (fm_op_s::tile, rcap)
 };
 
 template <typename T>
@@ -248,6 +249,8 @@ static fm_status run_fft(const FftJob& J, const Fused& F, const View& in, const 
   if (J.L <= fft_max_tile<T>() && !small) {
     if (ctx.dry) return FM_OK;
     FftArgs<T> a;
+    a.tile = J.tile;
+    a.rcap = J.rcap;
     a.L = J.L;
     a.conv = J.conv;
     a.dir0 = J.conv ? -1 : J.dir;
@@ -302,6 +305,8 @@ static fm_status run_fft(const FftJob& J, const Fused& F, const View& in, const 
   // pass A
   {
     FftArgs<T> a;
+    a.tile = J.tile;
+    a.rcap = J.rcap;
     a.small = small ? 1 : 0;
     a.L = N1;
     a.dir0 = dirA;
@@ -341,6 +346,8 @@ static fm_status run_fft(const FftJob& J, const Fused& F, const View& in, const 
   // pass B
   {
     FftArgs<T> a;
+    a.tile = J.tile;
+    a.rcap = J.rcap;
     a.small = small ? 1 : 0;
     a.L = N2;
     a.tw = tw_table<T>(ctx);
@@ -393,6 +400,8 @@ static fm_status run_fft(const FftJob& J, const Fused& F, const View& in, const 
   // pass C
   {
     FftArgs<T> a;
+    a.tile = J.tile;
+    a.rcap = J.rcap;
     a.small = small ? 1 : 0;
     a.L = N1;
     a.dir0 = +1;
@@ -449,6 +458,8 @@ static fm_status exec_fft_leaf(const fm_op_s* A, bool adj, const Fused& F, const
   J.Lin = in_len(A, adj);
   J.Lout = out_len(A, adj);
   J.real = group_real(A, F);
+  J.tile = A->tile;
+  J.rcap = A->rcap;
   const bool dbl = is_double(in.dt);
   if (A->kind == K_FOURIER) {
     J.conv = 0;

@@ -35,6 +35,8 @@ struct FftArgs {
   int64_t ncu = 0, ncols = 0, outer = 1, inner = 1;
   int V = 1, logV = 0;
   int small = 0;            // 1: small tiles (passes of a small two-pass FP64 problem)
+  int tile = 0;             // tile shape of strided views: 0 automatic, 1 default tile, 2 wide tile
+  int rcap = 0;             // 3: radices of at most 8 (compiled for FP32 tiles of 2^9 .. 2^12)
   // input view
   const void* in = nullptr;
   int64_t in_ld = 0, in_ostride = 0, in_tstride = 1;

@@ -234,9 +234,14 @@ __device__ __forceinline__ void p2_compute(C (&r)[EPT], int dir, const C* __rest
 
 // FRESH: the first pass's inputs came from global memory, so no thread can still be reading the
 // exchange buffer when the first pass writes it (the barrier before that write is skipped).
-template <typename C, bool VF, int THREADS, int EPT, int LOGL, int LOGV, int P, bool INV, bool FRESH = false>
+// LM: cap of log2 of the radix (0: the largest radix a thread's EPT elements hold).
+template <int EPT, int LM>
+__host__ __device__ constexpr int radix_cap() { return LM > 0 && LM < ept_lmax<EPT>() ? LM : ept_lmax<EPT>(); }
+
+template <typename C, bool VF, int THREADS, int EPT, int LOGL, int LOGV, int P, bool INV, bool FRESH = false,
+          int LM = 0>
 __device__ __forceinline__ void p2_run(C (&r)[EPT], C* s, int dir, const C* tw) {
-  using S = Sched<LOGL, ept_lmax<EPT>()>;
+  using S = Sched<LOGL, radix_cap<EPT, LM>()>;
   if constexpr (P < S::NR) {
     constexpr int LR = INV ? S::lr(S::NR - 1 - P) : S::lr(P);
     constexpr int LOGNS = INV ? S::ns_inv(P) : S::ns_fwd(P);
@@ -247,7 +252,7 @@ __device__ __forceinline__ void p2_run(C (&r)[EPT], C* s, int dir, const C* tw) 
       p2_write<C, VF, THREADS, EPT, LOGL, LOGV, LR, LOGNS>(r, s);
       __syncthreads();
     }
-    p2_run<C, VF, THREADS, EPT, LOGL, LOGV, P + 1, INV, FRESH>(r, s, dir, tw);
+    p2_run<C, VF, THREADS, EPT, LOGL, LOGV, P + 1, INV, FRESH, LM>(r, s, dir, tw);
   }
 }
 
@@ -368,23 +373,23 @@ __host__ __device__ constexpr int fft2_min_blocks() {
 
 // The exchange buffer (none when a single radix pass does the whole transform in
 // registers), then the per-vector table.
-template <typename C, int LOGL, int EPT>
+template <typename C, int LOGL, int EPT, int LM = 0>
 __host__ __device__ constexpr size_t fft2_vinfo_offset(int E) {
-  return Sched<LOGL, ept_lmax<EPT>()>::NR > 1 ? fft_vinfo_offset<C>(E) : 0;
+  return Sched<LOGL, radix_cap<EPT, LM>()>::NR > 1 ? fft_vinfo_offset<C>(E) : 0;
 }
 
 // SIMPLE: no fused operation on either side (complex in and out, natural index, no map,
 // diagonal, twiddle, scale or accumulation): loads and stores are a base plus a stride.
 // CONV: transform, spectrum product, inverse transform (circulant and Toeplitz products).
-template <typename T, int LOGL, int THREADS, int EPT, bool VF, bool SIMPLE, bool CONV>
+template <typename T, int LOGL, int THREADS, int EPT, bool VF, bool SIMPLE, bool CONV, int LM = 0>
 __global__ void __launch_bounds__(THREADS, fft2_min_blocks<T, LOGL, THREADS, EPT, CONV>())
     fft2_kernel(const __grid_constant__ FftArgs<T> a) {
   typedef typename Cx<T>::t C;
   constexpr int E = THREADS * EPT, LOGE = ilog2c(E), LOGV = LOGE - LOGL, V = 1 << LOGV;
-  using S = Sched<LOGL, ept_lmax<EPT>()>;
+  using S = Sched<LOGL, radix_cap<EPT, LM>()>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
-  VecInfo* vinfo = reinterpret_cast<VecInfo*>(smem_raw + fft2_vinfo_offset<C, LOGL, EPT>(E));
+  VecInfo* vinfo = reinterpret_cast<VecInfo*>(smem_raw + fft2_vinfo_offset<C, LOGL, EPT, LM>(E));
   const int64_t g0 = (int64_t)blockIdx.x * V;
   const int64_t nvec = a.ncu * a.outer * a.inner;
   pdl_launch_dependents();
@@ -421,7 +426,7 @@ __global__ void __launch_bounds__(THREADS, fft2_min_blocks<T, LOGL, THREADS, EPT
   constexpr int LRL = S::lr(S::NR - 1);
   C r[EPT];
   load_first<T, VF, SIMPLE, THREADS, EPT, LOGL, LOGV, LR0>(r, a, vinfo);
-  p2_run<C, VF, THREADS, EPT, LOGL, LOGV, 0, false, true>(r, s, a.dir0, a.tw);
+  p2_run<C, VF, THREADS, EPT, LOGL, LOGV, 0, false, true, LM>(r, s, a.dir0, a.tw);
   if constexpr (CONV) {
     // spectrum product at the natural positions t = j + k L/R of the last forward radix
     constexpr int R = 1 << LRL;
@@ -437,7 +442,7 @@ __global__ void __launch_bounds__(THREADS, fft2_min_blocks<T, LOGL, THREADS, EPT
         r[q * R + k] = cmul(r[q * R + k], a.spec_conj ? cconj(w) : w);
       }
     }
-    p2_run<C, VF, THREADS, EPT, LOGL, LOGV, 0, true>(r, s, -a.dir0, a.tw);
+    p2_run<C, VF, THREADS, EPT, LOGL, LOGV, 0, true, false, LM>(r, s, -a.dir0, a.tw);
     store_last<T, VF, SIMPLE, THREADS, EPT, LOGL, LOGV, LR0>(r, a, vinfo);
   } else {
     store_last<T, VF, SIMPLE, THREADS, EPT, LOGL, LOGV, LRL>(r, a, vinfo);
@@ -455,9 +460,9 @@ template <int LOGL, int MODE> struct TileCfg {
   static constexpr int EPT = (1 << LOGE) / THREADS;
 };
 
-template <typename T, int LOGL, int THREADS, int EPT, bool VF, bool SIMPLE, bool CONV>
+template <typename T, int LOGL, int THREADS, int EPT, bool VF, bool SIMPLE, bool CONV, int LM>
 fm_status fft2_start(const FftArgs<T>& a, int64_t tiles, size_t smem, cudaStream_t st) {
-  auto kern = fft2_kernel<T, LOGL, THREADS, EPT, VF, SIMPLE, CONV>;
+  auto kern = fft2_kernel<T, LOGL, THREADS, EPT, VF, SIMPLE, CONV, LM>;
   int dev = 0;
   cudaGetDevice(&dev);
   static std::atomic<unsigned long long> attr_bytes[32];
@@ -469,19 +474,25 @@ fm_status fft2_start(const FftArgs<T>& a, int64_t tiles, size_t smem, cudaStream
   // the kernel's label in errors and traces: element type, length, layout, convolution
   static const std::string label = std::string("fft2_kernel<") + (sizeof(T) == 4 ? "f32" : "f64") + ",L=2^" +
                                    std::to_string(LOGL) + (VF ? ",strided" : "") + (SIMPLE ? "" : ",fused") +
-                                   (CONV ? ",conv" : "") + ">";
+                                   (CONV ? ",conv" : "") + (LM ? ",radix<=" + std::to_string(1 << LM) : "") +
+                                   ">";
   return pdl_go(label.c_str(), kern, dim3((unsigned)tiles), dim3(THREADS), smem, st, a);
 }
 
-template <typename T, int LOGL, int THREADS, int EPT, bool VF>
+template <typename T, int LOGL, int THREADS, int EPT, bool VF, int LM>
 fm_status fft2_pick(const FftArgs<T>& a, bool simple, int64_t tiles, size_t smem, cudaStream_t st) {
   if (a.conv) {
-    return simple ? fft2_start<T, LOGL, THREADS, EPT, VF, true, true>(a, tiles, smem, st)
-                  : fft2_start<T, LOGL, THREADS, EPT, VF, false, true>(a, tiles, smem, st);
+    return simple ? fft2_start<T, LOGL, THREADS, EPT, VF, true, true, LM>(a, tiles, smem, st)
+                  : fft2_start<T, LOGL, THREADS, EPT, VF, false, true, LM>(a, tiles, smem, st);
   }
-  return simple ? fft2_start<T, LOGL, THREADS, EPT, VF, true, false>(a, tiles, smem, st)
-                : fft2_start<T, LOGL, THREADS, EPT, VF, false, false>(a, tiles, smem, st);
+  return simple ? fft2_start<T, LOGL, THREADS, EPT, VF, true, false, LM>(a, tiles, smem, st)
+                : fft2_start<T, LOGL, THREADS, EPT, VF, false, false, LM>(a, tiles, smem, st);
 }
+
+// The radix-capped schedules (radix <= 8) are compiled for the FP32 tiles of 2^9 .. 2^12, the
+// lengths of the benchmarked passes; elsewhere the cap is ignored.
+template <typename T, int LOGL>
+constexpr bool has_rcap_variant() { return sizeof(T) == 4 && LOGL >= 9 && LOGL <= 12; }
 
 template <typename T, int LOGL, int MODE>
 fm_status fft2_launch_cfg(FftArgs<T> a, cudaStream_t st) {
@@ -507,14 +518,24 @@ fm_status fft2_launch_cfg(FftArgs<T> a, cudaStream_t st) {
   }
   a.in_vcontig = (a.inner > 1 || a.in_ostride == 1) ? 1 : 0;
   a.out_vcontig = (a.inner > 1 || a.out_ostride == 1) ? 1 : 0;
-  const size_t smem = fft2_vinfo_offset<C, LOGL, EPT>(E) + (size_t)V * sizeof(VecInfo);
+  const bool capped = has_rcap_variant<T, LOGL>() && a.rcap == 3 && ept_lmax<EPT>() > 3;
+  const size_t smem = (capped ? fft2_vinfo_offset<C, LOGL, EPT, 3>(E) : fft2_vinfo_offset<C, LOGL, EPT>(E)) +
+                      (size_t)V * sizeof(VecInfo);
   const bool simple = a.in_mode == IO_C && a.out_mode == IO_C && !a.pre_map && !a.pre_dc && !a.pre_dr &&
                       !a.pre_tw && !a.post_tw && !a.post_dc && !a.post_dr && !a.post_map && a.scale == (T)1 &&
                       !a.beta && a.in_fmul == 1 && a.in_fmod == 1 && a.out_fmul == 1 && a.out_fmod == 1;
-  if constexpr (V > 1) {
-    if (a.in_vcontig) return fft2_pick<T, LOGL, THREADS, EPT, true>(a, simple, tiles, smem, st);
+  if constexpr (has_rcap_variant<T, LOGL>() && ept_lmax<EPT>() > 3) {
+    if (capped) {
+      if constexpr (V > 1) {
+        if (a.in_vcontig) return fft2_pick<T, LOGL, THREADS, EPT, true, 3>(a, simple, tiles, smem, st);
+      }
+      return fft2_pick<T, LOGL, THREADS, EPT, false, 3>(a, simple, tiles, smem, st);
+    }
   }
-  return fft2_pick<T, LOGL, THREADS, EPT, false>(a, simple, tiles, smem, st);
+  if constexpr (V > 1) {
+    if (a.in_vcontig) return fft2_pick<T, LOGL, THREADS, EPT, true, 0>(a, simple, tiles, smem, st);
+  }
+  return fft2_pick<T, LOGL, THREADS, EPT, false, 0>(a, simple, tiles, smem, st);
 }
 
 template <typename T, int LOGL>
@@ -526,7 +547,10 @@ fm_status fft2_launch(FftArgs<T> a, cudaStream_t st) {
     if (a.small) return fft2_launch_cfg<T, LOGL, 2>(a, st);
   }
   if constexpr (LOGL >= 9 && LOGL + 4 <= maxloge) {
-    if (a.inner >= 16) return fft2_launch_cfg<T, LOGL, 1>(a, st);
+    // wide tiles for strided views by default (a.tile 0); a.tile 1 forces the default tile and
+    // 2 the wide one (the calibration's choice)
+    const bool wide = a.tile == 2 ? a.inner > 1 : (a.tile == 1 ? false : a.inner >= 16);
+    if (wide) return fft2_launch_cfg<T, LOGL, 1>(a, st);
   }
   return fft2_launch_cfg<T, LOGL, 0>(a, st);
 }

@@ -523,7 +523,10 @@ struct fm_batch_s {
   int device = 0;
   FInst* inst = nullptr;
   int32_t* order = nullptr;
-  FGroup* groups = nullptr;        // persistent work list
+  FGroup* groups = nullptr;        // persistent work list, largest instances first
+  int32_t* order_asc = nullptr;    // ... and its smallest-first form (fm_batch_tune)
+  FGroup* groups_asc = nullptr;
+  int order_mode = 0;              // 0 largest first, 1 smallest first
   FGroup* single = nullptr;        // one group per instance (per-instance launches)
   std::vector<int32_t> single_index;  // instance -> its entry in `single`
   int ngroups = 0, nsingle = 0;
@@ -534,7 +537,7 @@ struct fm_batch_s {
 };
 
 static void batch_free(fm_batch_s* B) {
-  void* bufs[] = {B->inst, B->order, B->groups, B->single, B->y, B->tw2, B->counter};
+  void* bufs[] = {B->inst, B->order, B->groups, B->order_asc, B->groups_asc, B->single, B->y, B->tw2, B->counter};
   for (void* p : bufs)
     if (p) cudaFree(p);
   for (auto* o : B->ops) op_release(o);
@@ -582,15 +585,23 @@ fm_status fm_batch_create(const fm_op* A, int64_t count, void* stream, fm_batch*
   std::vector<int32_t> order(count);
   for (int64_t i = 0; i < count; ++i) order[i] = (int32_t)i;
   std::stable_sort(order.begin(), order.end(), [&](int32_t p, int32_t q) { return h[p].logn > h[q].logn; });
-  std::vector<FGroup> groups;
-  for (int64_t i = 0; i < count;) {
-    const int logn = h[order[i]].logn;
-    const int V = 1 << (14 - logn);
-    int c = 0;
-    while (i + c < count && c < V && h[order[i + c]].logn == logn) ++c;
-    groups.push_back({logn, c, (int)i, 0});
-    i += c;
-  }
+  auto make_groups = [&](const std::vector<int32_t>& ord) {
+    std::vector<FGroup> g;
+    for (int64_t i = 0; i < count;) {
+      const int logn = h[ord[i]].logn;
+      const int V = 1 << (14 - logn);
+      int c = 0;
+      while (i + c < count && c < V && h[ord[i + c]].logn == logn) ++c;
+      g.push_back({logn, c, (int)i, 0});
+      i += c;
+    }
+    return g;
+  };
+  const std::vector<FGroup> groups = make_groups(order);
+  std::vector<int32_t> order_asc(count);
+  for (int64_t i = 0; i < count; ++i) order_asc[i] = (int32_t)i;
+  std::stable_sort(order_asc.begin(), order_asc.end(), [&](int32_t p, int32_t q) { return h[p].logn < h[q].logn; });
+  const std::vector<FGroup> groups_asc = make_groups(order_asc);
   std::vector<FGroup> single(count);
   std::vector<int32_t> single_index(count);
   for (int64_t r = 0; r < count; ++r) {
@@ -615,6 +626,12 @@ fm_status fm_batch_create(const fm_op* A, int64_t count, void* stream, fm_batch*
   if (e == cudaSuccess) e = cudaMalloc(&B->order, sizeof(int32_t) * count);
   if (e == cudaSuccess) e = cudaMalloc(&B->groups, sizeof(FGroup) * groups.size());
   if (e == cudaSuccess) e = cudaMalloc(&B->single, sizeof(FGroup) * count);
+  if (e == cudaSuccess) e = cudaMalloc(&B->order_asc, sizeof(int32_t) * count);
+  if (e == cudaSuccess) e = cudaMalloc(&B->groups_asc, sizeof(FGroup) * groups_asc.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(B->order_asc, order_asc.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(B->groups_asc, groups_asc.data(), sizeof(FGroup) * groups_asc.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&B->y, sizeof(float) * xcol);
   if (e == cudaSuccess) e = cudaMalloc(&B->tw2, sizeof(float2) * 32768);
   if (e == cudaSuccess) e = cudaMalloc(&B->counter, sizeof(int));
@@ -687,6 +704,8 @@ static fm_status fista_run(fm_batch B, const float* b, float* x, const float* co
   a.inst = B->inst;
   a.order = B->order;
   a.b = b;
+  const bool asc = B->order_mode == 1 && p->mode == 0;
+  if (asc) a.order = B->order_asc;
   a.x = x;
   a.bp = bp;
   a.xp = xp;
@@ -708,7 +727,7 @@ static fm_status fista_run(fm_batch B, const float* b, float* x, const float* co
   a.counter = B->counter;
   const size_t smem = fista_smem();
   if (p->mode == 0) {
-    a.groups = B->groups;
+    a.groups = asc ? B->groups_asc : B->groups;
     a.ngroups = B->ngroups;
     a.single_group = -1;
     FM_CUDA(cudaMemsetAsync(B->counter, 0, sizeof(int), st));
@@ -739,6 +758,44 @@ fm_status fm_fista_batch(fm_batch B, const float* b, float* x, float* y, const f
   FM_TRY(check_params(p, rep));
   if (p->warm && !y) { set_error("a warm start needs the momentum state y of the run it resumes"); return FM_ERR_INVALID_ARG; }
   return fista_run(B, b, x, nullptr, nullptr, y, p, rep, (cudaStream_t)stream);
+}
+
+fm_status fm_batch_set_order(fm_batch B, int32_t order) {
+  clear_error();
+  if (!B || (order != 0 && order != 1)) { set_error("order 0 (largest first) or 1 (smallest first)"); return FM_ERR_INVALID_ARG; }
+  B->order_mode = order;
+  return FM_OK;
+}
+
+fm_status fm_batch_tune(fm_batch B, const float* b, float* x, const fm_fista_params* p, void* stream, float* ms,
+                        int32_t* chosen) {
+  clear_error();
+  if (!B || !b || !x || !p) { set_error("null pointer"); return FM_ERR_INVALID_ARG; }
+  FM_TRY(check_params(p, nullptr));
+  if (p->warm || p->mode != 0) { set_error("tune a cold persistent solve (warm = 0, mode = 0)"); return FM_ERR_INVALID_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  FM_CUDA(cudaEventCreate(&e0));
+  cudaError_t e = cudaEventCreate(&e1);
+  fm_status s = e == cudaSuccess ? FM_OK : FM_ERR_CUDA;
+  float t[2] = {0.f, 0.f};
+  const int start = B->order_mode;
+  for (int m = 0; m < 2 && s == FM_OK; ++m) {
+    B->order_mode = m;
+    s = fista_run(B, b, x, nullptr, nullptr, nullptr, p, nullptr, st);     // warm-up
+    if (s == FM_OK && cudaEventRecord(e0, st) != cudaSuccess) s = FM_ERR_CUDA;
+    if (s == FM_OK) s = fista_run(B, b, x, nullptr, nullptr, nullptr, p, nullptr, st);
+    if (s == FM_OK && cudaEventRecord(e1, st) != cudaSuccess) s = FM_ERR_CUDA;
+    if (s == FM_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t[m], e0, e1) != cudaSuccess))
+      s = FM_ERR_CUDA;
+  }
+  if (s == FM_ERR_CUDA) set_error("fm_batch_tune: CUDA error while timing");
+  B->order_mode = s == FM_OK ? (t[1] < t[0] ? 1 : 0) : start;
+  if (ms) { ms[0] = t[0]; ms[1] = t[1]; }
+  if (chosen) *chosen = B->order_mode;
+  cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return s;
 }
 
 fm_status fm_fista(const fm_op* A, int64_t batch, const float* const* b, float* const* x, const fm_fista_params* p,

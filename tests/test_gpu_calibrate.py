@@ -75,9 +75,10 @@ def test_calibrate_picks_a_candidate_and_stays_correct(fm, tmp_path):
     ref = O.Product(O.Partial(idx, n), O.Diag(d), O.Circulant(c))
     cache = str(tmp_path / "tune.json")
     res = A.calibrate(8, torch.complex64, cache=cache)
-    assert len(res) == 1 and res[0]["L"] == n
-    assert res[0]["n1"] in res[0]["ms"] and len(res[0]["ms"]) >= 2
-    assert all(v > 0 for v in res[0]["ms"].values())
+    assert [e["kind"] for e in res] == [0, 1, 2] and all(e["L"] == n for e in res)
+    for e in res:
+        assert e["value"] in e["ms"] and len(e["ms"]) >= 2
+        assert all(v > 0 for v in e["ms"].values())
     X = I.column_block(RNG, 2, n, np.complex64)
     Y = I.column_block(RNG, 2, n // 4, np.complex64)
     _check(A, ref, X, Y, 1e-5 * 18)
@@ -87,7 +88,8 @@ def test_calibrate_picks_a_candidate_and_stays_correct(fm, tmp_path):
     assert len(stored) == 1
     B = fm.product(fm.partial(idx, n), fm.diag(d), fm.circulant(c))
     again = B.calibrate(8, torch.complex64, cache=cache)
-    assert again[0]["n1"] == res[0]["n1"]
+    assert [(e["kind"], e["value"]) for e in again] == [(e["kind"], e["value"]) for e in res]
+    assert list(stored)[0].startswith(B.signature() + "|n=")
     _check(B, ref, X, Y, 1e-5 * 18)
 
 
@@ -99,4 +101,33 @@ def test_split_rules(fm):
         F.set_split(1 << 16, 4)           # N2 = 2^14 above one FP64 tile
     F.set_split(1 << 12, 64)              # no transform of that length: nothing to do
     F.set_split(1 << 16, 0)               # back to the default
-    assert fm.fourier(1024).calibrate(4) == []   # single-tile transforms: nothing to tune
+    # a single-tile transform has no split to tune, only its tile shape and radix schedule
+    assert [e["kind"] for e in fm.fourier(1024).calibrate(4)] == [1, 2]
+    with pytest.raises(fm.FmError):
+        F.set_plan(1 << 16, 2, 4)         # radix cap 0 or 3 only
+
+
+def _plan_cases(fm):
+    rng = np.random.default_rng(40)
+    c = I.cn(rng, (1024,))
+    K = fm.kron(fm.hadamard(4), fm.circulant(c), fm.fourier(16))
+    Kref = O.Kron(O.Hadamard(16), O.Circulant(c), O.Fourier(16))
+    c2, d2, idx2 = _cs(4096, 3)
+    P = fm.product(fm.partial(idx2, 4096), fm.diag(d2), fm.circulant(c2))
+    Pref = O.Product(O.Partial(idx2, 4096), O.Diag(d2), O.Circulant(c2))
+    F = fm.kron(fm.fourier(512), fm.fourier(32))
+    Fref = O.Kron(O.Fourier(512), O.Fourier(32))
+    return [(K, Kref, 1024), (P, Pref, 4096), (F, Fref, 512)]
+
+
+@pytest.mark.parametrize("tile,rcap", [(0, 0), (1, 0), (2, 0), (0, 3), (1, 3), (2, 3)])
+def test_every_plan_choice_keeps_parity(fm, tile, rcap):
+    # the compiled variants the calibration chooses among: tile shape of strided views and the
+    # radix schedule, on a Kron circulant of 2^10 along a stride, a 2^12 convolution tile and a
+    # 2^9 Fourier along a stride of 32
+    for A, ref, L in _plan_cases(fm):
+        A.set_plan(L, 1, tile)
+        A.set_plan(L, 2, rcap)
+        X = I.column_block(RNG, 3, A.cols, np.complex64)
+        Y = I.column_block(RNG, 3, A.rows, np.complex64)
+        _check(A, ref, X, Y, 1e-5 * 18)

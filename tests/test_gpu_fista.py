@@ -181,6 +181,27 @@ def test_fista_rejects_bad_resume_and_alignment(fm):
     assert e.value.status == 1
 
 
+def test_work_list_orders_and_tuning(fm):
+    # both work-list orders solve every instance to the oracle's answer, bit for bit alike, and
+    # the tuner times both and keeps one
+    insts = _sized(10, 17, 0) + _sized(12, 5, 100) + _sized(9, 4, 60)
+    B, b, bs = _batch(fm, insts)
+    B.set_order(0)
+    x0 = B.solve(b).clone()
+    B.set_order(1)
+    x1, rep = B.solve(b, report=True)
+    torch.cuda.synchronize()
+    assert torch.equal(x0, x1)
+    xs = _split(x1.cpu().numpy(), insts)
+    for i in (0, 16, 17, 21, 22):
+        xo = _oracle(insts[i], bs[i])[0]
+        assert np.linalg.norm(xs[i] - xo) / np.linalg.norm(xo) <= 1e-4
+    r = B.tune(b)
+    assert r["order"] in (0, 1) and all(t > 0 for t in r["ms"])
+    with pytest.raises(fm.FmError):
+        B.set_order(2)
+
+
 def test_batch_rejects_other_operators(fm):
     with pytest.raises(fm.FmError):
         fm.FistaBatch([fm.fourier(256)])
