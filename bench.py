@@ -52,6 +52,9 @@ HAD_APPLY_BYTES = 2 * HAD_N * HAD_K * 4
 # (dram__bytes_read.sum + dram__bytes_write.sum); None where no current capture exists.
 NCU_TRAFFIC = {
     "fwht_long_kernel": 90139392,
+    # captured on one column of the Kron workload, scaled x4 to a 4-column launch
+    "fft2_kernel<f32,L=2^10,strided,conv>": 4 * (134313472 + 91964160),
+    "kron_hf_kernel<8,6>": 4 * (134244608 + 85037056),
 }
 FISTA_INSTANCES = 4096
 FISTA_ITERS = 200
@@ -329,7 +332,7 @@ def main():
     ap.add_argument("--rows", type=int, default=1, help="also measure the other hot-path rows")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", default=None, choices=["hadamard", "hadamard_int8", "hadamard_bf16", "cs", "kron",
-                                                        "circulant_c128", "fista", "fourier"],
+                                                        "kron1", "circulant_c128", "fista", "fourier"],
                     help="run one workload a few times and exit (for ncu captures)")
     args = ap.parse_args()
     world, rank, local = dist_init()
@@ -687,8 +690,11 @@ def profile_run(fm, torch, dev, which, steps):
         Xg = torch.from_numpy(X).to(dev)
         A.calibrate(Xg.shape[0], torch.complex64)
         fn = lambda: A.forward(Xg)  # noqa: E731
-    elif which == "kron":
+    elif which in ("kron", "kron1"):
+        # kron1: column 0 only (the same kernels on a quarter of the tiles, for full captures)
         ck, Xk, _ = I.kron_large()
+        if which == "kron1":
+            Xk = Xk[:1].copy()
         A = fm.kron(fm.hadamard(8), fm.circulant(ck), fm.fourier(64))
         Xg = torch.from_numpy(Xk).to(dev)
         A.calibrate(Xg.shape[0], torch.complex64)   # as in the bench step
