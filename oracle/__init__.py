@@ -15,7 +15,11 @@ Every operator carries
                      convolution, Eq. (5); butterflies; mode products), in FP64,
                      with columns of ``X`` as vectors (shape ``[cols, K]``).
 
-``fista`` follows the accelerated proximal-gradient iteration step by step.
+``fista`` follows the accelerated proximal-gradient iteration step by step;
+``omp`` (module ``omp``) the greedy selection with a least-squares solve per
+step; ``gradients`` the parameter gradients of Diag, Circulant and Toeplitz;
+``ndt`` the block matrix and two-level Toeplitz of the ultrasound model;
+``lfsr`` the shift-register sequence of the LFSR circulant.
 
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests in
 ``tests/test_oracle_pins.py`` (definitions against independent library
