@@ -499,7 +499,7 @@ def main():
                        "l2": "inputs larger than L2: each 512 MiB buffer is 4x the L2, steps back to back",
                        "streams": "one stream (the operator's workspace is per operator)",
                        "plan": {"calibrated": kron_plan,
-                                "format": "[L, kind (0 split, 1 tile shape, 2 radix schedule), chosen value]"},
+                                "format": "[L, kind (0 split, 1 tile shape, 2 radix schedule, 3 fused Kron pass), chosen value]"},
                        "parallelism": f"replicas x{world}"},
             "clocks": clk.summary(),
             "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": KRON_N * KRON_K * 8,

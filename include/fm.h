@@ -251,9 +251,14 @@ fm_status fm_omp(fm_op A, const void* b, fm_dtype dt, int32_t K, void* x, int32_
  *           Toeplitz embedding of length L > 8192), N1 = 2^e with N1, N2 in [2^5, 2^13];
  *   kind 1  the tile shape of an FFT leaf's strided views: 0 automatic (wide tiles of 8 or 16
  *           vectors for inner strides >= 16), 1 the default tile (2^12 elements), 2 the wide
- *           tile wherever it applies (lengths 2^9 .. 2^10 in FP32, 2^9 in FP64);
+ *           tile wherever it applies (lengths 2^9 .. 2^10 in FP32, 2^9 in FP64), 3 the wide FP32
+ *           tile split into 4 groups of warps that transform their own vectors with barriers
+ *           of their own;
  *   kind 2  the radix schedule of an FFT leaf's tiles: 0 the per-length table (radix 16
- *           first), 3 radices of at most 8 (compiled for FP32 tiles of 2^9 .. 2^12).
+ *           first), 3 radices of at most 8 (compiled for FP32 tiles of 2^9 .. 2^12);
+ *   kind 3  the fused pass of a Kron(Hadamard, ..., Fourier) operator on complex64 columns (L =
+ *           the Kron's length): 0 one CTA per [2^a][2^b] tile, 1 each tile on a cluster of two
+ *           CTAs that exchange the last Hadamard digit through distributed shared memory.
  * fm_calibrate times A's forward + adjoint (one warm-up, mean of three) on ncols probe columns
  * of complex_of(dt) for every candidate of every setting of every transform in A, one setting
  * at a time (splits first, then per leaf the tile shape, then the radix schedule), and keeps
@@ -263,11 +268,11 @@ fm_status fm_omp(fm_op A, const void* b, fm_dtype dt, int32_t K, void* x, int32_
  * (optional) receives the number of tuned settings (0 for an operator without FFT leaves). */
 typedef struct {
   int64_t L;            /* transform length */
-  int64_t n1;           /* chosen value (kind 0: N1, N2 = L / N1; kind 1: tile shape; kind 2: radix cap) */
+  int64_t n1;           /* chosen value (kind 0: N1, N2 = L / N1; 1: tile shape; 2: radix cap; 3: Kron pass) */
   int32_t ncand;        /* candidates timed (<= 8) */
   int64_t cand_n1[8];   /* their values */
   float ms[8];          /* forward + adjoint of A with that value, milliseconds */
-  int32_t kind;         /* 0 split, 1 tile shape, 2 radix schedule */
+  int32_t kind;         /* 0 split, 1 tile shape, 2 radix schedule, 3 fused Kron pass */
 } fm_tune_entry;
 fm_status fm_calibrate(fm_op A, int64_t ncols, fm_dtype dt, void* stream, fm_tune_entry* report,
                        int32_t max_entries, int32_t* n_entries);
@@ -276,7 +281,8 @@ fm_status fm_calibrate(fm_op A, int64_t ncols, fm_dtype dt, void* stream, fm_tun
  * N1, L / N1 in [2^5, 2^13]; FM_OK if A has no transform of length L.  Same rules about
  * concurrent use as fm_calibrate. */
 fm_status fm_set_split(fm_op A, int64_t L, int64_t n1, void* stream);
-/* Set one plan setting (kind and value as in fm_tune_entry) of every FFT leaf of length L in A,
+/* Set one plan setting (kind and value as in fm_tune_entry) of every FFT leaf (kinds 1, 2) or fused
+ * Kron operator (kind 3) of length L in A,
  * e.g. to restore a cached calibration.  FM_ERR_INVALID_ARG for a value outside the kind's
  * range; FM_OK if A has no leaf of length L. */
 fm_status fm_set_plan(fm_op A, int64_t L, int32_t kind, int64_t value, void* stream);

@@ -144,7 +144,8 @@ class Op:
         With `cache` (a JSON file path) the choices are stored under `key` (default: the
         operator's signature, ncols, dtype and the GPU's SM count) and a later call with the
         same key restores them without timing.  Returns the list of {"L", "kind", "value", "ms"}
-        entries that were applied (kind 0 split, 1 tile shape, 2 radix schedule)."""
+        entries that were applied (kind 0 split, 1 tile shape, 2 radix schedule, 3 fused Kron
+        pass)."""
         import json
         import os
         sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count

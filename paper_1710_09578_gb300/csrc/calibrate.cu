@@ -51,6 +51,16 @@ void collect_fft(fm_op_s* A, std::vector<fm_op_s*>& out) {
   for (fm_op_s* k : A->kids) collect_fft(k, out);
 }
 
+// Kron operators whose outer Hadamard and inner Fourier factors run as one fused pass.
+void collect_kron(fm_op_s* A, std::vector<fm_op_s*>& out) {
+  if (!A) return;
+  if (A->kind == K_KRON && A->kids.size() >= 2 && A->kids[0]->kind == K_HADAMARD &&
+      A->kids[0]->had_mode == FM_HAD_FP32 && A->kids.back()->kind == K_FOURIER) {
+    if (std::find(out.begin(), out.end(), A) == out.end()) out.push_back(A);
+  }
+  for (fm_op_s* k : A->kids) collect_kron(k, out);
+}
+
 void signature(const fm_op_s* A, std::string& out) {
   static const char* names[] = {"F", "C", "T", "H", "D", "P", "Prod", "Sum", "BlkDiag", "Kron", "Herm", "Blocks"};
   out += names[A->kind];
@@ -118,9 +128,18 @@ fm_status fm_set_plan(fm_op A, int64_t L, int32_t kind, int64_t value, void* str
   clear_error();
   if (!A) { set_error("null operator"); return FM_ERR_INVALID_ARG; }
   if (kind == 0) return fm_set_split(A, L, value, stream);
-  if ((kind == 1 && (value < 0 || value > 2)) || (kind == 2 && value != 0 && value != 3) || kind < 0 || kind > 2) {
-    set_error("plan setting %d = %lld: tile shape 0..2, radix cap 0 or 3", kind, (long long)value);
+  if ((kind == 1 && (value < 0 || value > 3)) || (kind == 2 && value != 0 && value != 3) ||
+      (kind == 3 && value != 0 && value != 1) || kind < 0 || kind > 3) {
+    set_error("plan setting %d = %lld: tile shape 0..3, radix cap 0 or 3, fused Kron pass 0 or 1", kind,
+              (long long)value);
     return FM_ERR_INVALID_ARG;
+  }
+  if (kind == 3) {
+    std::vector<fm_op_s*> kr;
+    collect_kron(A, kr);
+    for (fm_op_s* k : kr)
+      if (k->rows == L) k->tile = (int)value;
+    return FM_OK;
   }
   std::vector<fm_op_s*> fl;
   collect_fft(A, fl);
@@ -145,10 +164,11 @@ fm_status fm_calibrate(fm_op A, int64_t ncols, fm_dtype dt, void* stream, fm_tun
   if (n_entries) *n_entries = 0;
   if (!A || ncols <= 0) { set_error("bad argument"); return FM_ERR_INVALID_ARG; }
   if (dt != FM_F32 && dt != FM_F64 && dt != FM_C64 && dt != FM_C128) { set_error("calibration dtype"); return FM_ERR_DTYPE; }
-  std::vector<fm_op_s*> leaves, fleaves;
+  std::vector<fm_op_s*> leaves, fleaves, krons;
   collect(A, leaves);
   collect_fft(A, fleaves);
-  if (leaves.empty() && fleaves.empty()) return FM_OK;
+  collect_kron(A, krons);
+  if (leaves.empty() && fleaves.empty() && krons.empty()) return FM_OK;
   cudaStream_t st = (cudaStream_t)stream;
   const fm_dtype cdt = complex_of(dt);
   const size_t esz = (size_t)dtype_size(cdt);
@@ -221,19 +241,28 @@ fm_status fm_calibrate(fm_op A, int64_t ncols, fm_dtype dt, void* stream, fm_tun
     if (report && done < max_entries) report[done] = ent;
     ++done;
   }
-  // the plan of each FFT leaf's tiles: tile shape of strided views, then the radix cap
-  std::vector<fm_op_s*> fl;
-  collect_fft(A, fl);
-  for (fm_op_s* leaf : fl) {
+  // the plan of each FFT leaf's tiles (tile shape of strided views, then the radix cap), and of
+  // each fused Kron pass (one CTA or a CTA pair per tile)
+  struct Setting {
+    fm_op_s* op;
+    int kind;
+  };
+  std::vector<Setting> settings;
+  for (fm_op_s* leaf : fleaves) settings.push_back({leaf, 1}), settings.push_back({leaf, 2});
+  for (fm_op_s* k : krons) settings.push_back({k, 3});
+  for (const Setting& set : settings) {
     if (s != FM_OK) break;
-    for (int kind = 1; kind <= 2 && s == FM_OK; ++kind) {
-      int* field = kind == 1 ? &leaf->tile : &leaf->rcap;
-      const std::vector<int> cand = kind == 1 ? std::vector<int>{0, 1, 2} : std::vector<int>{0, 3};
+    {
+      fm_op_s* leaf = set.op;
+      const int kind = set.kind;
+      int* field = kind == 2 ? &leaf->rcap : &leaf->tile;
+      const std::vector<int> cand = kind == 1 ? std::vector<int>{0, 1, 2, 3}
+                                  : kind == 2 ? std::vector<int>{0, 3} : std::vector<int>{0, 1};
       const int start = *field;
       int best = start;
       float best_ms = 0.f;
       fm_tune_entry ent = {};
-      ent.L = leaf->L;
+      ent.L = kind == 3 ? leaf->rows : leaf->L;
       ent.kind = kind;
       for (int c : cand) {
         *field = c;

@@ -35,7 +35,7 @@ struct FftArgs {
   int64_t ncu = 0, ncols = 0, outer = 1, inner = 1;
   int V = 1, logV = 0;
   int small = 0;            // 1: small tiles (passes of a small two-pass FP64 problem)
-  int tile = 0;             // tile shape of strided views: 0 automatic, 1 default tile, 2 wide tile
+  int tile = 0;             // tile shape of strided views: 0 automatic, 1 default, 2 wide, 3 wide in 4 groups
   int rcap = 0;             // 3: radices of at most 8 (compiled for FP32 tiles of 2^9 .. 2^12)
   // input view
   const void* in = nullptr;

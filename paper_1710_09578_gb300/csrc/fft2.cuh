@@ -81,10 +81,11 @@ __device__ __forceinline__ int sp2(int t, int v) {
   return lin + (lin >> 4);
 }
 
-// Butterfly q of this thread in a radix-2^LR pass: vector v, index j in [0, L/R).
+// Butterfly q of this thread in a radix-2^LR pass: vector v, index j in [0, L/R).  THREADS is
+// the size of the thread group that owns the tile (the whole CTA, or one of its groups).
 template <bool VF, int THREADS, int LOGL, int LOGV, int LR>
 __device__ __forceinline__ void bfly2(int q, int& j, int& v) {
-  const int b = threadIdx.x + q * THREADS;
+  const int b = (threadIdx.x & (THREADS - 1)) + q * THREADS;
   if (VF) {
     v = b & ((1 << LOGV) - 1);
     j = b >> LOGV;
@@ -234,12 +235,23 @@ __device__ __forceinline__ void p2_compute(C (&r)[EPT], int dir, const C* __rest
 
 // FRESH: the first pass's inputs came from global memory, so no thread can still be reading the
 // exchange buffer when the first pass writes it (the barrier before that write is skipped).
+// Barrier of the thread group that owns a tile: the whole CTA, or group threadIdx.x / THREADS
+// of BLOCK / THREADS groups with a named barrier of its own (ids 1, 2, ...).
+template <int THREADS, int BLOCK>
+__device__ __forceinline__ void tile_sync() {
+  if constexpr (THREADS == BLOCK) {
+    __syncthreads();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)(threadIdx.x / THREADS)), "r"(THREADS) : "memory");
+  }
+}
+
 // LM: cap of log2 of the radix (0: the largest radix a thread's EPT elements hold).
 template <int EPT, int LM>
 __host__ __device__ constexpr int radix_cap() { return LM > 0 && LM < ept_lmax<EPT>() ? LM : ept_lmax<EPT>(); }
 
 template <typename C, bool VF, int THREADS, int EPT, int LOGL, int LOGV, int P, bool INV, bool FRESH = false,
-          int LM = 0>
+          int LM = 0, int BLOCK = THREADS>
 __device__ __forceinline__ void p2_run(C (&r)[EPT], C* s, int dir, const C* tw) {
   using S = Sched<LOGL, radix_cap<EPT, LM>()>;
   if constexpr (P < S::NR) {
@@ -248,11 +260,11 @@ __device__ __forceinline__ void p2_run(C (&r)[EPT], C* s, int dir, const C* tw) 
     if constexpr (P > 0) p2_read<C, VF, THREADS, EPT, LOGL, LOGV, LR>(r, s);
     p2_compute<C, VF, THREADS, EPT, LOGL, LOGV, LR, LOGNS>(r, dir, tw);
     if constexpr (P + 1 < S::NR) {
-      if constexpr (!(FRESH && P == 0)) __syncthreads();
+      if constexpr (!(FRESH && P == 0)) tile_sync<THREADS, BLOCK>();
       p2_write<C, VF, THREADS, EPT, LOGL, LOGV, LR, LOGNS>(r, s);
-      __syncthreads();
+      tile_sync<THREADS, BLOCK>();
     }
-    p2_run<C, VF, THREADS, EPT, LOGL, LOGV, P + 1, INV, FRESH, LM>(r, s, dir, tw);
+    p2_run<C, VF, THREADS, EPT, LOGL, LOGV, P + 1, INV, FRESH, LM, BLOCK>(r, s, dir, tw);
   }
 }
 
@@ -381,7 +393,9 @@ __host__ __device__ constexpr size_t fft2_vinfo_offset(int E) {
 // SIMPLE: no fused operation on either side (complex in and out, natural index, no map,
 // diagonal, twiddle, scale or accumulation): loads and stores are a base plus a stride.
 // CONV: transform, spectrum product, inverse transform (circulant and Toeplitz products).
-template <typename T, int LOGL, int THREADS, int EPT, bool VF, bool SIMPLE, bool CONV, int LM = 0>
+// G > 1: the tile's V vectors are split into G groups of V / G, each transformed by THREADS / G
+// threads with barriers of their own (the groups never wait for one another).
+template <typename T, int LOGL, int THREADS, int EPT, bool VF, bool SIMPLE, bool CONV, int LM = 0, int G = 1>
 __global__ void __launch_bounds__(THREADS, fft2_min_blocks<T, LOGL, THREADS, EPT, CONV>())
     fft2_kernel(const __grid_constant__ FftArgs<T> a) {
   typedef typename Cx<T>::t C;
@@ -424,17 +438,23 @@ __global__ void __launch_bounds__(THREADS, fft2_min_blocks<T, LOGL, THREADS, EPT
 
   constexpr int LR0 = S::lr(0);
   constexpr int LRL = S::lr(S::NR - 1);
+  // this thread's group: its threads, its vectors and its part of the exchange buffer
+  static_assert(G >= 1 && V % G == 0 && THREADS / G >= 32, "groups of whole warps and whole vectors");
+  constexpr int TG = THREADS / G, LOGVG = LOGV - ilog2c(G), EG = E / G;
+  const int grp = G > 1 ? (int)(threadIdx.x / TG) : 0;
+  C* sg = s + grp * (EG + EG / 16);
+  const VecInfo* vg = vinfo + grp * (V / G);
   C r[EPT];
-  load_first<T, VF, SIMPLE, THREADS, EPT, LOGL, LOGV, LR0>(r, a, vinfo);
-  p2_run<C, VF, THREADS, EPT, LOGL, LOGV, 0, false, true, LM>(r, s, a.dir0, a.tw);
+  load_first<T, VF, SIMPLE, TG, EPT, LOGL, LOGVG, LR0>(r, a, vg);
+  p2_run<C, VF, TG, EPT, LOGL, LOGVG, 0, false, true, LM, THREADS>(r, sg, a.dir0, a.tw);
   if constexpr (CONV) {
     // spectrum product at the natural positions t = j + k L/R of the last forward radix
     constexpr int R = 1 << LRL;
 #pragma unroll
     for (int q = 0; q < EPT / R; ++q) {
       int j, v;
-      bfly2<VF, THREADS, LOGL, LOGV, LRL>(q, j, v);
-      const C* sp = a.spec + vinfo[v].soff + j;
+      bfly2<VF, TG, LOGL, LOGVG, LRL>(q, j, v);
+      const C* sp = a.spec + vg[v].soff + j;
 #pragma unroll
       for (int k = 0; k < R; ++k) {
         // the spectrum is written once at construction: read-only path
@@ -442,10 +462,10 @@ __global__ void __launch_bounds__(THREADS, fft2_min_blocks<T, LOGL, THREADS, EPT
         r[q * R + k] = cmul(r[q * R + k], a.spec_conj ? cconj(w) : w);
       }
     }
-    p2_run<C, VF, THREADS, EPT, LOGL, LOGV, 0, true, false, LM>(r, s, -a.dir0, a.tw);
-    store_last<T, VF, SIMPLE, THREADS, EPT, LOGL, LOGV, LR0>(r, a, vinfo);
+    p2_run<C, VF, TG, EPT, LOGL, LOGVG, 0, true, false, LM, THREADS>(r, sg, -a.dir0, a.tw);
+    store_last<T, VF, SIMPLE, TG, EPT, LOGL, LOGVG, LR0>(r, a, vg);
   } else {
-    store_last<T, VF, SIMPLE, THREADS, EPT, LOGL, LOGV, LRL>(r, a, vinfo);
+    store_last<T, VF, SIMPLE, TG, EPT, LOGL, LOGVG, LRL>(r, a, vg);
   }
 }
 
@@ -460,9 +480,9 @@ template <int LOGL, int MODE> struct TileCfg {
   static constexpr int EPT = (1 << LOGE) / THREADS;
 };
 
-template <typename T, int LOGL, int THREADS, int EPT, bool VF, bool SIMPLE, bool CONV, int LM>
+template <typename T, int LOGL, int THREADS, int EPT, bool VF, bool SIMPLE, bool CONV, int LM, int G>
 fm_status fft2_start(const FftArgs<T>& a, int64_t tiles, size_t smem, cudaStream_t st) {
-  auto kern = fft2_kernel<T, LOGL, THREADS, EPT, VF, SIMPLE, CONV, LM>;
+  auto kern = fft2_kernel<T, LOGL, THREADS, EPT, VF, SIMPLE, CONV, LM, G>;
   int dev = 0;
   cudaGetDevice(&dev);
   static std::atomic<unsigned long long> attr_bytes[32];
@@ -475,18 +495,18 @@ fm_status fft2_start(const FftArgs<T>& a, int64_t tiles, size_t smem, cudaStream
   static const std::string label = std::string("fft2_kernel<") + (sizeof(T) == 4 ? "f32" : "f64") + ",L=2^" +
                                    std::to_string(LOGL) + (VF ? ",strided" : "") + (SIMPLE ? "" : ",fused") +
                                    (CONV ? ",conv" : "") + (LM ? ",radix<=" + std::to_string(1 << LM) : "") +
-                                   ">";
+                                   (G > 1 ? ",groups=" + std::to_string(G) : "") + ">";
   return pdl_go(label.c_str(), kern, dim3((unsigned)tiles), dim3(THREADS), smem, st, a);
 }
 
-template <typename T, int LOGL, int THREADS, int EPT, bool VF, int LM>
+template <typename T, int LOGL, int THREADS, int EPT, bool VF, int LM, int G = 1>
 fm_status fft2_pick(const FftArgs<T>& a, bool simple, int64_t tiles, size_t smem, cudaStream_t st) {
   if (a.conv) {
-    return simple ? fft2_start<T, LOGL, THREADS, EPT, VF, true, true, LM>(a, tiles, smem, st)
-                  : fft2_start<T, LOGL, THREADS, EPT, VF, false, true, LM>(a, tiles, smem, st);
+    return simple ? fft2_start<T, LOGL, THREADS, EPT, VF, true, true, LM, G>(a, tiles, smem, st)
+                  : fft2_start<T, LOGL, THREADS, EPT, VF, false, true, LM, G>(a, tiles, smem, st);
   }
-  return simple ? fft2_start<T, LOGL, THREADS, EPT, VF, true, false, LM>(a, tiles, smem, st)
-                : fft2_start<T, LOGL, THREADS, EPT, VF, false, false, LM>(a, tiles, smem, st);
+  return simple ? fft2_start<T, LOGL, THREADS, EPT, VF, true, false, LM, G>(a, tiles, smem, st)
+                : fft2_start<T, LOGL, THREADS, EPT, VF, false, false, LM, G>(a, tiles, smem, st);
 }
 
 // The radix-capped schedules (radix <= 8) are compiled for the FP32 tiles of 2^9 .. 2^12, the
@@ -533,6 +553,10 @@ fm_status fft2_launch_cfg(FftArgs<T> a, cudaStream_t st) {
     }
   }
   if constexpr (V > 1) {
+    // tile shape 3: the wide strided tile in 4 independent groups (FP32 wide tiles only)
+    if constexpr (MODE == 1 && sizeof(T) == 4 && V % 4 == 0 && THREADS / 4 >= 32) {
+      if (a.tile == 3 && a.in_vcontig) return fft2_pick<T, LOGL, THREADS, EPT, true, 0, 4>(a, simple, tiles, smem, st);
+    }
     if (a.in_vcontig) return fft2_pick<T, LOGL, THREADS, EPT, true, 0>(a, simple, tiles, smem, st);
   }
   return fft2_pick<T, LOGL, THREADS, EPT, false, 0>(a, simple, tiles, smem, st);
@@ -549,7 +573,7 @@ fm_status fft2_launch(FftArgs<T> a, cudaStream_t st) {
   if constexpr (LOGL >= 9 && LOGL + 4 <= maxloge) {
     // wide tiles for strided views by default (a.tile 0); a.tile 1 forces the default tile and
     // 2 the wide one (the calibration's choice)
-    const bool wide = a.tile == 2 ? a.inner > 1 : (a.tile == 1 ? false : a.inner >= 16);
+    const bool wide = a.tile >= 2 ? a.inner > 1 : (a.tile == 1 ? false : a.inner >= 16);
     if (wide) return fft2_launch_cfg<T, LOGL, 1>(a, st);
   }
   return fft2_launch_cfg<T, LOGL, 0>(a, st);

@@ -190,7 +190,8 @@ struct fm_op_s {
   // two-pass plan for long transforms
   fm::BigPlan big;
   // execution plan of the tile transforms (fm_set_plan / fm_calibrate): tile shape of strided
-  // views (0 automatic, 1 default tile, 2 wide tile) and radix cap (0 schedule table, 3 radix <= 8)
+  // views (0 automatic, 1 default tile, 2 wide tile, 3 wide tile in 4 groups) and radix cap (0
+  // schedule table, 3 radix <= 8)
   int tile = 0, rcap = 0;
   // dense execution of a small leaf (fm_set_dense): the matrix, column-major rows x cols
   int dense = 0;

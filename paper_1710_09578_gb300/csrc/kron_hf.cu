@@ -90,6 +90,142 @@ __global__ void __launch_bounds__(1 << (LA + LB - 4), 1) kron_hf_kernel(const __
   hrounds<THREADS, EPT, LA, LB, 0>(r, s, a, out);
 }
 
+// ---- the same pass with each tile split over a cluster of two CTAs
+// CTA rank r of the pair holds rows [2^(LA-1) r, 2^(LA-1) (r + 1)) of the [2^LA][2^LB] tile (half
+// the shared memory, so two pairs' CTAs share an SM and one pair's loads overlap the other's
+// arithmetic).  Each CTA runs the row Fourier transforms and H_{2^(LA-1)} over its rows; the
+// last Hadamard digit (H_2 across the halves) combines both halves: rank r writes columns
+// [2^(LB-1) r, 2^(LB-1) (r + 1)) of all rows, reading the partner's half of those columns from
+// its shared memory (distributed shared memory, a quarter of the tile per CTA).  Cluster
+// barriers (hardware barriers, no polling) order the halves before and after the exchange.
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ float2 ld_dsmem(const float2* local_ptr, unsigned rank) {
+  const unsigned addr = (unsigned)__cvta_generic_to_shared(local_ptr);
+  unsigned remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(addr), "r"(rank));
+  float2 v;
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(remote) : "memory");
+  return v;
+}
+
+// every round of H_{2^LAL} over the rows of the tile in shared memory, results written back
+template <int THREADS, int EPT, int LAL, int LB, int P>
+__device__ __forceinline__ void hrounds_local(float2 (&r)[EPT], float2* s) {
+  using Rd = WRound<LAL, P>;
+  constexpr int R = 1 << Rd::RB;
+#pragma unroll
+  for (int q = 0; q < EPT / R; ++q) {
+    int v;
+    const int t0 = wgroup<THREADS, LB, Rd::SH, Rd::RB>(q, v);
+#pragma unroll
+    for (int k = 0; k < R; ++k) r[q * R + k] = s[wsp<LB>(t0 + (k << Rd::SH), v)];
+    wht_group<float2, R>(&r[q * R]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < EPT / R; ++q) {
+    int v;
+    const int t0 = wgroup<THREADS, LB, Rd::SH, Rd::RB>(q, v);
+#pragma unroll
+    for (int k = 0; k < R; ++k) s[wsp<LB>(t0 + (k << Rd::SH), v)] = r[q * R + k];
+  }
+  __syncthreads();
+  if constexpr (P + 1 < Rd::NR) hrounds_local<THREADS, EPT, LAL, LB, P + 1>(r, s);
+}
+
+template <int LA, int LB>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(1 << (LA + LB - 5), 2)
+    kron_hf2_kernel(const __grid_constant__ KronHFArgs a) {
+  constexpr int LAL = LA - 1, THREADS = 1 << (LA + LB - 5), EPT = 16;
+  constexpr int ROWS = 1 << LAL, COLS = 1 << LB, HALF = COLS / 2;
+  using S = Sched<LB>;
+  constexpr int LR0 = S::lr(0), LRL = S::lr(S::NR - 1);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* s = reinterpret_cast<float2*>(smem_raw);
+  const unsigned rank = cluster_rank();
+  const int64_t tile = blockIdx.x >> 1;
+  const int64_t col = tile / a.nmid, mid = tile % a.nmid;
+  const float2* in = a.in + col * a.in_ld + (mid << LB) + (int64_t)rank * ROWS * a.sa;
+  float2* out = a.out + col * a.out_ld + (mid << LB);
+  float2 r[EPT];
+  pdl_launch_dependents();
+  pdl_wait();
+  // Fourier along this CTA's rows: first pass straight from HBM
+  {
+    constexpr int R = 1 << LR0, M = 1 << (LB - LR0);
+#pragma unroll
+    for (int q = 0; q < EPT / R; ++q) {
+      int j, v;
+      bfly2<false, THREADS, LB, LAL, LR0>(q, j, v);
+      const float2* p = in + (int64_t)v * a.sa + j;
+#pragma unroll
+      for (int k = 0; k < R; ++k) r[q * R + k] = gld(p + k * M);
+    }
+  }
+  p2_run<float2, false, THREADS, EPT, LB, LAL, 0, false, true>(r, s, a.dir, a.tw);
+  __syncthreads();
+  p2_write<float2, false, THREADS, EPT, LB, LAL, LRL, LB - LRL>(r, s);
+  __syncthreads();
+  hrounds_local<THREADS, EPT, LAL, LB, 0>(r, s);
+  // the last digit across the pair: top = rank 0's rows, bottom = rank 1's rows
+  cluster_sync();
+  const unsigned peer = rank ^ 1u;
+  constexpr int RSTEP = THREADS / HALF;
+  const int c = (int)rank * HALF + (int)(threadIdx.x % HALF);
+  const int i0 = (int)(threadIdx.x / HALF);
+  float2 top[ROWS / RSTEP], bot[ROWS / RSTEP];
+#pragma unroll
+  for (int k = 0; k < ROWS / RSTEP; ++k) {
+    const float2* mine = s + wsp<LB>(i0 + k * RSTEP, c);
+    const float2 own = *mine;
+    const float2 oth = ld_dsmem(mine, peer);
+    top[k] = rank == 0 ? own : oth;
+    bot[k] = rank == 0 ? oth : own;
+  }
+#pragma unroll
+  for (int k = 0; k < ROWS / RSTEP; ++k) {
+    const int i = i0 + k * RSTEP;
+    float2* p0 = out + (int64_t)i * a.sa + c;
+    float2* p1 = out + (int64_t)(i + ROWS) * a.sa + c;
+    float2 y0 = cscale(cadd(top[k], bot[k]), a.scale);
+    float2 y1 = cscale(csub(top[k], bot[k]), a.scale);
+    if (a.beta) {
+      y0 = cadd(y0, gld(p0));
+      y1 = cadd(y1, gld(p1));
+    }
+    gst(p0, y0);
+    gst(p1, y1);
+  }
+  // the partner reads this CTA's shared memory until it passes this barrier
+  cluster_sync();
+}
+
+template <int LA, int LB>
+fm_status hf2_start(const KronHFArgs& a, cudaStream_t st) {
+  constexpr int E = 1 << (LA - 1 + LB);
+  constexpr size_t smem = (size_t)(E + E / 16 + 1) * sizeof(float2);
+  auto kern = kron_hf2_kernel<LA, LB>;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  static std::atomic<unsigned> attr_set{0};
+  if (dev < 32 && !(attr_set.load() & (1u << dev))) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) { set_error("kron_hf2 smem attribute: %s", cudaGetErrorString(e)); return FM_ERR_CUDA; }
+    attr_set.fetch_or(1u << dev);
+  }
+  if (a.ntiles == 0) return FM_OK;
+  if (a.ntiles > 0x3fffffffLL) { set_error("kron_hf2: too many tiles"); return FM_ERR_UNSUPPORTED; }
+  static const std::string label = "kron_hf2_kernel<" + std::to_string(LA) + "," + std::to_string(LB) + ">";
+  return pdl_go(label.c_str(), kern, dim3((unsigned)(2 * a.ntiles)), dim3(1 << (LA + LB - 5)), smem, st, a);
+}
+
 template <int LA, int LB>
 fm_status hf_start(const KronHFArgs& a, cudaStream_t st) {
   constexpr int E = 1 << (LA + LB);
@@ -115,7 +251,7 @@ bool kron_hf_ok(int la, int lb) { return la >= 4 && la <= 8 && lb >= 4 && lb <= 
 
 fm_status kron_hf_launch(const KronHFArgs& a, int la, int lb, cudaStream_t st) {
 #define FM_HF(A, B) \
-  if (la == A && lb == B) return hf_start<A, B>(a, st);
+  if (la == A && lb == B) return a.pair ? hf2_start<A, B>(a, st) : hf_start<A, B>(a, st);
   FM_HF(4, 6) FM_HF(5, 5) FM_HF(6, 4)
   FM_HF(4, 7) FM_HF(5, 6) FM_HF(6, 5) FM_HF(7, 4)
   FM_HF(4, 8) FM_HF(5, 7) FM_HF(6, 6) FM_HF(7, 5) FM_HF(8, 4)

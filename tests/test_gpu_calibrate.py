@@ -105,6 +105,8 @@ def test_split_rules(fm):
     assert [e["kind"] for e in fm.fourier(1024).calibrate(4)] == [1, 2]
     with pytest.raises(fm.FmError):
         F.set_plan(1 << 16, 2, 4)         # radix cap 0 or 3 only
+    with pytest.raises(fm.FmError):
+        F.set_plan(1 << 16, 1, 4)         # tile shapes 0 .. 3
 
 
 def _plan_cases(fm):
@@ -120,7 +122,7 @@ def _plan_cases(fm):
     return [(K, Kref, 1024), (P, Pref, 4096), (F, Fref, 512)]
 
 
-@pytest.mark.parametrize("tile,rcap", [(0, 0), (1, 0), (2, 0), (0, 3), (1, 3), (2, 3)])
+@pytest.mark.parametrize("tile,rcap", [(0, 0), (1, 0), (2, 0), (3, 0), (0, 3), (1, 3), (2, 3), (3, 3)])
 def test_every_plan_choice_keeps_parity(fm, tile, rcap):
     # the compiled variants the calibration chooses among: tile shape of strided views and the
     # radix schedule, on a Kron circulant of 2^10 along a stride, a 2^12 convolution tile and a

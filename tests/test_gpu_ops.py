@@ -420,9 +420,10 @@ def test_kron_hadamard_strided_axis(fm, dt, la, lb):
     assert colerr(got, 2 * ref.apply(X.T.astype(np.complex128)).T) <= tol32(n)
 
 
+@pytest.mark.parametrize("pair", [0, 1])
 @pytest.mark.parametrize("la,mid,lb,ortho", [(4, 4, 6, 0), (6, 3, 4, 1), (7, 2, 6, 0), (5, 1, 5, 0), (8, 1, 6, 1),
                                           (4, 1, 8, 0)])
-def test_kron_hadamard_fourier_fused(fm, la, mid, lb, ortho):
+def test_kron_hadamard_fourier_fused(fm, la, mid, lb, ortho, pair):
     # Kron(H, middle, F) on complex64: the outer Hadamard and inner Fourier factors run as
     # one fused pass (middle = 1: no middle factor, the pass writes the output directly)
     c = I.cn(RNG, (mid,))
@@ -433,11 +434,12 @@ def test_kron_hadamard_fourier_fused(fm, la, mid, lb, ortho):
     kids = [fm.hadamard(la)] + mk + [fm.fourier(1 << lb, ortho=bool(ortho))]
     refs = [O.Hadamard(1 << la)] + mr + [O.Fourier(1 << lb, ortho=bool(ortho))]
     A = fm.kron(*kids)
+    A.set_plan(A.rows, 3, pair)        # one CTA per tile, or a CTA pair per tile
     ref = O.Kron(*refs)
     n = ref.cols
     both(fm, A, ref, blk(3, n, np.complex64), blk(3, n, np.complex64), tol32(n))
     X = blk(2, n, np.complex64)
-    got = fm.sum_(A, A).forward(gpu(X)).cpu().numpy()       # the second term accumulates
+    got = fm.sum_(A, A).forward(gpu(X)).cpu().numpy()       # the second term accumulates (same plan)
     assert colerr(got, 2 * ref.apply(X.T).T) <= tol32(n)
 
 
@@ -461,11 +463,13 @@ def test_kron_workload_analogue(fm):
     assert colerr(got, (D @ X.T).T) <= tol32(4096)
 
 
-def test_kron_workload_full_sampled(fm):
+@pytest.mark.parametrize("pair", [0, 1])
+def test_kron_workload_full_sampled(fm, pair):
     # Kron(H_256, C_1024, F_64) on 4 columns of length 2^24: sampled rows from the
-    # definition and the adjoint identity at full size.
+    # definition and the adjoint identity at full size (both forms of the fused pass).
     c, X, Y = I.kron_large()
     A = fm.kron(fm.hadamard(8), fm.circulant(c), fm.fourier(64))
+    A.set_plan(A.rows, 3, pair)
     ref = O.Kron(O.Hadamard(256), O.Circulant(c), O.Fourier(64))
     Xg, Yg = gpu(X), gpu(Y)
     F = A.forward(Xg)
