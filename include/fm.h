@@ -257,8 +257,8 @@ fm_status fm_omp(fm_op A, const void* b, fm_dtype dt, int32_t K, void* x, int32_
  *   kind 2  the radix schedule of an FFT leaf's tiles: 0 the per-length table (radix 16
  *           first), 3 radices of at most 8 (compiled for FP32 tiles of 2^9 .. 2^12);
  *   kind 3  the fused pass of a Kron(Hadamard, ..., Fourier) operator on complex64 columns (L =
- *           the Kron's length): 0 one CTA per [2^a][2^b] tile, 1 each tile on a cluster of two
- *           CTAs that exchange the last Hadamard digit through distributed shared memory.
+ *           the Kron's length): 0 one CTA per [2^a][2^b] tile; 1 each tile on a cluster of two
+ *           CTAs that combine the last Hadamard digit through distributed shared memory.
  * fm_calibrate times A's forward + adjoint (one warm-up, mean of three) on ncols probe columns
  * of complex_of(dt) for every candidate of every setting of every transform in A, one setting
  * at a time (splits first, then per leaf the tile shape, then the radix schedule), and keeps

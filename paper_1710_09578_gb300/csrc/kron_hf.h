@@ -18,7 +18,7 @@ struct KronHFArgs {
   float scale = 1.f;              // 1, or 1/sqrt(2^LB) for the orthonormal Fourier matrix
   int beta = 0;                   // 1: accumulate into out
   const float2* tw = nullptr;     // pass-twiddle tables (pass_tw_offset)
-  int pair = 0;                   // 1: each tile on a cluster of two CTAs (kron_hf2_kernel)
+  int pair = 0;                   // each tile on one CTA (0) or a cluster of two CTAs (1)
 };
 
 // Tiles [2^la][2^lb] with 2^10 <= 2^(la+lb) <= 2^14 and 4 <= la, lb <= 8.
