@@ -258,7 +258,9 @@ fm_status fm_omp(fm_op A, const void* b, fm_dtype dt, int32_t K, void* x, int32_
  *           first), 3 radices of at most 8 (compiled for FP32 tiles of 2^9 .. 2^12);
  *   kind 3  the fused pass of a Kron(Hadamard, ..., Fourier) operator on complex64 columns (L =
  *           the Kron's length): 0 one CTA per [2^a][2^b] tile; 1 each tile on a cluster of two
- *           CTAs that combine the last Hadamard digit through distributed shared memory.
+ *           CTAs that combine the last Hadamard digit through distributed shared memory; 2 a
+ *           cluster of four CTAs and the last two digits (tiles of at least 2^11 elements; a
+ *           smaller tile takes the pair).
  * fm_calibrate times A's forward + adjoint (one warm-up, mean of three) on ncols probe columns
  * of complex_of(dt) for every candidate of every setting of every transform in A, one setting
  * at a time (splits first, then per leaf the tile shape, then the radix schedule), and keeps

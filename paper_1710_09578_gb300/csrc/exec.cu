@@ -741,7 +741,7 @@ static fm_status exec_kron(const fm_op_s* A, bool adj, const View& in, const Vie
       h.scale = fl->ortho ? (float)(1.0 / std::sqrt((double)fl->L)) : 1.f;
       h.beta = k > 2 ? 0 : beta;
       h.tw = tw_table<float>(ctx);
-      h.pair = A->tile == 1 ? 1 : 0;   // the Kron operator's plan: one CTA or a CTA pair per tile
+      h.pair = A->tile;   // the Kron operator's plan: one CTA, a pair or a quad of CTAs per tile
       FM_TRY(kron_hf_launch(h, la, lb, ctx.st));
     }
     if (k == 2) {

@@ -248,11 +248,13 @@ fm_status hfc_start(const KronHFArgs& a, cudaStream_t st) {
 template <int LA, int LB>
 fm_status hf_start(const KronHFArgs& a, cudaStream_t st);
 
-// one CTA per tile, or a cluster of two (the kernel is written for CL = 2 or 4; the 4-CTA form
-// is not launched: it faulted on the 2^24 x 4 workload with no cause found in its indexing)
+// the forms a tile shape admits: CTA pairs for every shape, quads where a CTA keeps whole warps
 template <int LA, int LB>
 fm_status hf_pick(const KronHFArgs& a, cudaStream_t st) {
-  if (a.pair == 1) return hfc_start<LA, LB, 2>(a, st);
+  if (a.pair == 2) {
+    if constexpr (LA + LB >= 11) return hfc_start<LA, LB, 4>(a, st);
+  }
+  if (a.pair >= 1) return hfc_start<LA, LB, 2>(a, st);
   return hf_start<LA, LB>(a, st);
 }
 

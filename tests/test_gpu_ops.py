@@ -420,7 +420,7 @@ def test_kron_hadamard_strided_axis(fm, dt, la, lb):
     assert colerr(got, 2 * ref.apply(X.T.astype(np.complex128)).T) <= tol32(n)
 
 
-@pytest.mark.parametrize("pair", [0, 1])
+@pytest.mark.parametrize("pair", [0, 1, 2])
 @pytest.mark.parametrize("la,mid,lb,ortho", [(4, 4, 6, 0), (6, 3, 4, 1), (7, 2, 6, 0), (5, 1, 5, 0), (8, 1, 6, 1),
                                           (4, 1, 8, 0)])
 def test_kron_hadamard_fourier_fused(fm, la, mid, lb, ortho, pair):
@@ -434,7 +434,7 @@ def test_kron_hadamard_fourier_fused(fm, la, mid, lb, ortho, pair):
     kids = [fm.hadamard(la)] + mk + [fm.fourier(1 << lb, ortho=bool(ortho))]
     refs = [O.Hadamard(1 << la)] + mr + [O.Fourier(1 << lb, ortho=bool(ortho))]
     A = fm.kron(*kids)
-    A.set_plan(A.rows, 3, pair)        # one CTA per tile, or a CTA pair per tile
+    A.set_plan(A.rows, 3, pair)        # one CTA, a pair or a quad of CTAs per tile
     ref = O.Kron(*refs)
     n = ref.cols
     both(fm, A, ref, blk(3, n, np.complex64), blk(3, n, np.complex64), tol32(n))
@@ -463,7 +463,7 @@ def test_kron_workload_analogue(fm):
     assert colerr(got, (D @ X.T).T) <= tol32(4096)
 
 
-@pytest.mark.parametrize("pair", [0, 1])
+@pytest.mark.parametrize("pair", [0, 1, 2])
 def test_kron_workload_full_sampled(fm, pair):
     # Kron(H_256, C_1024, F_64) on 4 columns of length 2^24: sampled rows from the
     # definition and the adjoint identity at full size (both forms of the fused pass).
