@@ -54,7 +54,7 @@ NCU_TRAFFIC = {
     "fwht_long_kernel": 90139392,
     # captured on one column of the Kron workload, scaled x4 to a 4-column launch
     "fft2_kernel<f32,L=2^10,strided,conv>": 4 * (134313472 + 91964160),
-    "kron_hf_kernel<8,6>": 4 * (134244608 + 85037056),
+    "kron_hfc_kernel<8,6,cluster=2>": 4 * (134260736 + 85292544),
 }
 FISTA_INSTANCES = 4096
 FISTA_ITERS = 200
