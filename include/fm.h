@@ -249,11 +249,13 @@ fm_status fm_omp(fm_op A, const void* b, fm_dtype dt, int32_t K, void* x, int32_
  * it chooses, among variants compiled into the library:
  *   kind 0  the split L = N1 x N2 of a transform longer than one tile (Fourier, Circulant or
  *           Toeplitz embedding of length L > 8192), N1 = 2^e with N1, N2 in [2^5, 2^13];
- *   kind 1  the tile shape of an FFT leaf's strided views: 0 automatic (wide tiles of 8 or 16
- *           vectors for inner strides >= 16), 1 the default tile (2^12 elements), 2 the wide
- *           tile wherever it applies (lengths 2^9 .. 2^10 in FP32, 2^9 in FP64), 3 the wide FP32
- *           tile split into 4 groups of warps that transform their own vectors with barriers
- *           of their own;
+ *   kind 1  the tile shape of an FFT leaf's strided views: 0 automatic (for inner strides >= 16
+ *           radix-32 tiles at length 2^10 in FP32, wide tiles of 8 or 16 vectors elsewhere), 1
+ *           the default tile (2^12 elements), 2 the wide tile wherever it applies (lengths 2^9
+ *           .. 2^10 in FP32, 2^9 in FP64), 3 the wide FP32 tile split into 4 groups of warps that
+ *           transform their own vectors with barriers of their own, 4 radix-32 tiles (FP32
+ *           lengths 2^9 and 2^10, strided or not: 2^13 elements, 256 threads of 32 elements, so
+ *           a transform takes two radix passes instead of three);
  *   kind 2  the radix schedule of an FFT leaf's tiles: 0 the per-length table (radix 16
  *           first), 3 radices of at most 8 (compiled for FP32 tiles of 2^9 .. 2^12);
  *   kind 3  the fused pass of a Kron(Hadamard, ..., Fourier) operator on complex64 columns (L =

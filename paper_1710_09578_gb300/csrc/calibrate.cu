@@ -128,9 +128,9 @@ fm_status fm_set_plan(fm_op A, int64_t L, int32_t kind, int64_t value, void* str
   clear_error();
   if (!A) { set_error("null operator"); return FM_ERR_INVALID_ARG; }
   if (kind == 0) return fm_set_split(A, L, value, stream);
-  if ((kind == 1 && (value < 0 || value > 3)) || (kind == 2 && value != 0 && value != 3) ||
+  if ((kind == 1 && (value < 0 || value > 4)) || (kind == 2 && value != 0 && value != 3) ||
       (kind == 3 && (value < 0 || value > 2)) || kind < 0 || kind > 3) {
-    set_error("plan setting %d = %lld: tile shape 0..3, radix cap 0 or 3, fused Kron pass 0..2", kind,
+    set_error("plan setting %d = %lld: tile shape 0..4, radix cap 0 or 3, fused Kron pass 0..2", kind,
               (long long)value);
     return FM_ERR_INVALID_ARG;
   }
@@ -256,7 +256,7 @@ fm_status fm_calibrate(fm_op A, int64_t ncols, fm_dtype dt, void* stream, fm_tun
       fm_op_s* leaf = set.op;
       const int kind = set.kind;
       int* field = kind == 2 ? &leaf->rcap : &leaf->tile;
-      const std::vector<int> cand = kind == 1 ? std::vector<int>{0, 1, 2, 3}
+      const std::vector<int> cand = kind == 1 ? std::vector<int>{0, 1, 2, 3, 4}
                                   : kind == 2 ? std::vector<int>{0, 3} : std::vector<int>{0, 1, 2};
       const int start = *field;
       int best = start;

@@ -46,19 +46,20 @@ __host__ __device__ constexpr int sched_cap_lr(int logl, int lmax, int p) {
              ? logl / sched_cap_nr(logl, lmax) + (p < logl % sched_cap_nr(logl, lmax) ? 1 : 0)
              : 0;
 }
-// log2 of the largest radix a thread with EPT elements can hold (at most 16).
+// log2 of the largest radix a thread with EPT elements can hold (at most 32).
 template <int EPT>
 __host__ __device__ constexpr int ept_lmax() {
-  return EPT >= 16 ? 4 : (EPT >= 8 ? 3 : (EPT >= 4 ? 2 : 1));
+  return EPT >= 32 ? 5 : (EPT >= 16 ? 4 : (EPT >= 8 ? 3 : (EPT >= 4 ? 2 : 1)));
 }
 
+// Radix 32 (threads of 32 elements): as few passes as radix 32 allows, balanced.
 template <int LOGL, int LMAX = 4>
 struct Sched {
   static_assert(LOGL >= 1 && LOGL <= 14, "transform length 2^1 .. 2^14 per tile");
-  static_assert(LMAX >= 1 && LMAX <= 4, "radix 2 .. 16");
-  static constexpr int NR = LMAX >= 4 ? sched_nr(LOGL) : sched_cap_nr(LOGL, LMAX);
+  static_assert(LMAX >= 1 && LMAX <= 5, "radix 2 .. 32");
+  static constexpr int NR = LMAX == 4 ? sched_nr(LOGL) : sched_cap_nr(LOGL, LMAX);
   __host__ __device__ static constexpr int lr(int p) {
-    return LMAX >= 4 ? sched_lr(LOGL, p) : sched_cap_lr(LOGL, LMAX, p);
+    return LMAX == 4 ? sched_lr(LOGL, p) : sched_cap_lr(LOGL, LMAX, p);
   }
   // log2 Ns before forward pass q (radices in order) and before inverse pass q (reversed)
   __host__ __device__ static constexpr int ns_fwd(int q) {
@@ -75,11 +76,25 @@ struct Sched {
 
 // Shared-memory word of element t of tile vector v (VF: vectors fastest), one pad slot
 // every 16 words.
-template <bool VF, int LOGL, int LOGV>
+//
+// SW: the layout of the radix-32 tiles of 2^10 (8 vectors), whose two exchanges write the
+// elements t = 32 j + k (k < 32) of butterfly j and read t = j + 32 k.  With t = 32 th + tl,
+// word = 264 th + 8 tl + v (VF) or 1056 v + 33 th + tl: both patterns step a register by a
+// constant, and in each half-warp (two values of th, or of tl, times 8 vectors; or 16 of them)
+// the 8-byte words fall in 16 distinct bank pairs, where the padded layout put four butterflies
+// on the same 8 pairs.
+template <bool VF, int LOGL, int LOGV, bool SW = false>
 __device__ __forceinline__ int sp2(int t, int v) {
-  const int lin = VF ? ((t << LOGV) + v) : ((v << LOGL) + t);
-  return lin + (lin >> 4);
+  if constexpr (SW) {
+    static_assert(LOGL == 10 && LOGV == 3, "radix-32 layout: 8 vectors of 2^10");
+    return VF ? ((t >> 5) * 264 + (t & 31) * 8 + v) : (v * 1056 + (t >> 5) * 33 + (t & 31));
+  } else {
+    const int lin = VF ? ((t << LOGV) + v) : ((v << LOGL) + t);
+    return lin + (lin >> 4);
+  }
 }
+template <int EPT, int LOGL, int LOGV>
+__host__ __device__ constexpr bool sw_layout() { return EPT >= 32 && LOGL == 10 && LOGV == 3; }
 
 // Butterfly q of this thread in a radix-2^LR pass: vector v, index j in [0, L/R).  THREADS is
 // the size of the thread group that owns the tile (the whole CTA, or one of its groups).
@@ -97,11 +112,21 @@ __device__ __forceinline__ void bfly2(int q, int& j, int& v) {
 
 // Elements t0 + k DT (k < R) of vector v: when the word step is a multiple of 16 the pad
 // slots between two of them are a constant too, so the addresses are one base plus
-// compile-time offsets.
-template <bool VF, int LOGL, int LOGV, int DT, int R, typename C>
+// compile-time offsets (in the SW layout, DT = 1 from t0 = 32 j and DT = 32 from t0 < 32, the
+// steps are constants by construction).
+template <int DT, bool VF, int LOGV>
+__host__ __device__ constexpr int sw_step() {
+  return DT == 1 ? (VF ? (1 << LOGV) : 1) : (VF ? 264 : 33);
+}
+template <bool VF, int LOGL, int LOGV, int DT, int R, bool SW, typename C>
 __device__ __forceinline__ void s_gather(C* x, const C* s, int t0, int v) {
   constexpr int S = VF ? (DT << LOGV) : DT;
-  if constexpr (S % 16 == 0) {
+  if constexpr (SW) {
+    static_assert(DT == 1 || DT == 32, "radix-32 layout: the two exchanges of a 2^10 tile");
+    const C* p = s + sp2<VF, LOGL, LOGV, true>(t0, v);
+#pragma unroll
+    for (int k = 0; k < R; ++k) x[k] = p[k * sw_step<DT, VF, LOGV>()];
+  } else if constexpr (S % 16 == 0) {
     const C* p = s + sp2<VF, LOGL, LOGV>(t0, v);
 #pragma unroll
     for (int k = 0; k < R; ++k) x[k] = p[k * (S + S / 16)];
@@ -110,10 +135,15 @@ __device__ __forceinline__ void s_gather(C* x, const C* s, int t0, int v) {
     for (int k = 0; k < R; ++k) x[k] = s[sp2<VF, LOGL, LOGV>(t0 + k * DT, v)];
   }
 }
-template <bool VF, int LOGL, int LOGV, int DT, int R, typename C>
+template <bool VF, int LOGL, int LOGV, int DT, int R, bool SW, typename C>
 __device__ __forceinline__ void s_scatter(const C* x, C* s, int t0, int v) {
   constexpr int S = VF ? (DT << LOGV) : DT;
-  if constexpr (S % 16 == 0) {
+  if constexpr (SW) {
+    static_assert(DT == 1 || DT == 32, "radix-32 layout: the two exchanges of a 2^10 tile");
+    C* p = s + sp2<VF, LOGL, LOGV, true>(t0, v);
+#pragma unroll
+    for (int k = 0; k < R; ++k) p[k * sw_step<DT, VF, LOGV>()] = x[k];
+  } else if constexpr (S % 16 == 0) {
     C* p = s + sp2<VF, LOGL, LOGV>(t0, v);
 #pragma unroll
     for (int k = 0; k < R; ++k) p[k * (S + S / 16)] = x[k];
@@ -130,7 +160,7 @@ __device__ __forceinline__ void p2_read(C (&r)[EPT], const C* s) {
   for (int q = 0; q < EPT / R; ++q) {
     int j, v;
     bfly2<VF, THREADS, LOGL, LOGV, LR>(q, j, v);
-    s_gather<VF, LOGL, LOGV, (1 << (LOGL - LR)), R>(&r[q * R], s, j, v);
+    s_gather<VF, LOGL, LOGV, (1 << (LOGL - LR)), R, sw_layout<EPT, LOGL, LOGV>()>(&r[q * R], s, j, v);
   }
 }
 
@@ -143,7 +173,7 @@ __device__ __forceinline__ void p2_write(const C (&r)[EPT], C* s) {
     int j, v;
     bfly2<VF, THREADS, LOGL, LOGV, LR>(q, j, v);
     const int base = ((j >> LOGNS) << (LOGNS + LR)) + (j & ((1 << LOGNS) - 1));
-    s_scatter<VF, LOGL, LOGV, (1 << LOGNS), R>(&r[q * R], s, base, v);
+    s_scatter<VF, LOGL, LOGV, (1 << LOGNS), R, sw_layout<EPT, LOGL, LOGV>()>(&r[q * R], s, base, v);
   }
 }
 
@@ -154,7 +184,7 @@ __device__ __forceinline__ void twiddle_powers(C* x, C w) {
   if constexpr (R == 2) {
     x[1] = cmul(x[1], w);
   } else {
-    C p[R];
+    C p[R < 16 ? R : (R == 16 ? 16 : 8)];
     p[1] = w;
     p[2] = cmul(w, w);
     p[3] = cmul(p[2], w);
@@ -169,8 +199,23 @@ __device__ __forceinline__ void twiddle_powers(C* x, C w) {
 #pragma unroll
       for (int k = 9; k < 16; ++k) p[k] = cmul(p[8], p[k - 8]);
     }
+    if constexpr (R == 32) {
+      // w^(8a + b) = w^(8a) w^b: eight low powers and three high ones live, not 31
+      const C w8 = cmul(p[4], p[4]);
 #pragma unroll
-    for (int k = 1; k < R; ++k) x[k] = cmul(x[k], p[k]);
+      for (int k = 1; k < 8; ++k) x[k] = cmul(x[k], p[k]);
+      C h = w8;
+#pragma unroll
+      for (int a = 1; a < 4; ++a) {
+        x[8 * a] = cmul(x[8 * a], h);
+#pragma unroll
+        for (int b = 1; b < 8; ++b) x[8 * a + b] = cmul(x[8 * a + b], cmul(h, p[b]));
+        if (a < 3) h = cmul(h, w8);
+      }
+    } else {
+#pragma unroll
+      for (int k = 1; k < R; ++k) x[k] = cmul(x[k], p[k]);
+    }
   }
 }
 
@@ -206,8 +251,12 @@ __device__ __forceinline__ void p2_compute(C (&r)[EPT], int dir, const C* __rest
     if (LOGNS > 0) {
       int j, v;
       bfly2<VF, THREADS, LOGL, LOGV, LR>(q, j, v);
-      const C* row = twp + pass_tw_offset(LOGNS + LR, LR) + ((int64_t)(j & ((1 << LOGNS) - 1)) << LR);
+      // (a radix-32 pass reads its base twiddle W_(Ns R)^(j mod Ns) from the radix-16 table of
+      // the same span: entry 1 of row j mod Ns there is the same power)
+      constexpr int LT = LR < 4 ? LR : 4;
+      const C* row = twp + pass_tw_offset(LOGNS + LR, LT) + ((int64_t)(j & ((1 << LOGNS) - 1)) << LT);
       if constexpr (sizeof(C) == 16) {
+        static_assert(LR <= 4, "radix-32 passes are compiled for FP32 tiles only");
         // FP64: every power from the table (a product tree of FP64 multiplies costs more)
         C w[R];
         tw_row<LR>(w, row);
@@ -226,7 +275,8 @@ __device__ __forceinline__ void p2_compute(C (&r)[EPT], int dir, const C* __rest
         twiddle_powers<C, R>(&r[q * R], w);
       }
     }
-    if (R == 16) dft16(&r[q * R], dir);
+    if (R == 32) dft32(&r[q * R], dir);
+    else if (R == 16) dft16(&r[q * R], dir);
     else if (R == 8) dft8(&r[q * R], dir);
     else if (R == 4) dft4(&r[q * R], dir);
     else dft2(&r[q * R]);
@@ -374,13 +424,14 @@ __device__ __forceinline__ void store_last(typename Cx<T>::t (&r)[EPT], const Ff
 // Resident CTAs per SM the register allocation is held to, for FP32 tiles: 4 x 256 threads
 // (32 warps per SM; at most a few registers spill), 3 x 256 for the convolution tiles of
 // 2^5, 2^6 and 2^9 (radix-8 passes with two butterflies per thread, whose spectrum product
-// would spill tens of bytes at 64 registers), 2 x 512 x 16; the 512 x 32 and FP64 tiles
-// need their registers.
+// would spill tens of bytes at 64 registers), 2 x 512 x 16 and 2 x 256 x 32 (radix-32
+// tiles, 128 registers); the 512 x 32 and FP64 tiles need their registers.
 template <typename T, int LOGL, int THREADS, int EPT, bool CONV>
 __host__ __device__ constexpr int fft2_min_blocks() {
   return sizeof(T) != 4 || THREADS < 256
              ? 1
-             : (THREADS <= 256 ? (CONV && (LOGL == 5 || LOGL == 6 || LOGL == 9) ? 3 : 4) : (EPT <= 16 ? 2 : 1));
+             : (THREADS <= 256 ? (EPT >= 32 ? 2 : (CONV && (LOGL == 5 || LOGL == 6 || LOGL == 9) ? 3 : 4))
+                               : (EPT <= 16 ? 2 : 1));
 }
 
 // The exchange buffer (none when a single radix pass does the whole transform in
@@ -471,12 +522,15 @@ __global__ void __launch_bounds__(THREADS, fft2_min_blocks<T, LOGL, THREADS, EPT
 
 // Tile shapes: 0 the default (2^12 elements, or one vector), 1 wide (16 vectors of a
 // strided view, 8 for 2^10 so that two CTAs of 16 elements per thread share an SM), 2 small (2^9 elements, four warps of 4 elements per thread: many CTAs for
-// small FP64 problems, with a warp on every SM sub-partition's FP64 unit).
+// small FP64 problems, with a warp on every SM sub-partition's FP64 unit), 4 radix 32 (FP32
+// 2^9 and 2^10: 2^13 elements, 256 threads of 32 elements, two passes per transform instead of
+// three).
 template <int LOGL, int MODE> struct TileCfg {
-  static constexpr int LOGE = MODE == 1 ? (LOGL + 4 > 13 ? 13 : (LOGL + 4 < 12 ? 12 : LOGL + 4))
+  static constexpr int LOGE = MODE == 4 ? 13
+                              : MODE == 1 ? (LOGL + 4 > 13 ? 13 : (LOGL + 4 < 12 ? 12 : LOGL + 4))
                               : MODE == 2 ? (LOGL < 9 ? 9 : LOGL)
                                           : (LOGL < 12 ? 12 : LOGL);
-  static constexpr int THREADS = MODE == 2 ? 128 : (LOGE <= 12 ? 256 : 512);
+  static constexpr int THREADS = MODE == 2 ? 128 : (MODE == 4 || LOGE <= 12 ? 256 : 512);
   static constexpr int EPT = (1 << LOGE) / THREADS;
 };
 
@@ -495,6 +549,7 @@ fm_status fft2_start(const FftArgs<T>& a, int64_t tiles, size_t smem, cudaStream
   static const std::string label = std::string("fft2_kernel<") + (sizeof(T) == 4 ? "f32" : "f64") + ",L=2^" +
                                    std::to_string(LOGL) + (VF ? ",strided" : "") + (SIMPLE ? "" : ",fused") +
                                    (CONV ? ",conv" : "") + (LM ? ",radix<=" + std::to_string(1 << LM) : "") +
+                                   (!LM && EPT >= 32 ? ",radix=32" : "") +
                                    (G > 1 ? ",groups=" + std::to_string(G) : "") + ">";
   return pdl_go(label.c_str(), kern, dim3((unsigned)tiles), dim3(THREADS), smem, st, a);
 }
@@ -538,13 +593,13 @@ fm_status fft2_launch_cfg(FftArgs<T> a, cudaStream_t st) {
   }
   a.in_vcontig = (a.inner > 1 || a.in_ostride == 1) ? 1 : 0;
   a.out_vcontig = (a.inner > 1 || a.out_ostride == 1) ? 1 : 0;
-  const bool capped = has_rcap_variant<T, LOGL>() && a.rcap == 3 && ept_lmax<EPT>() > 3;
+  const bool capped = MODE != 4 && has_rcap_variant<T, LOGL>() && a.rcap == 3 && ept_lmax<EPT>() > 3;
   const size_t smem = (capped ? fft2_vinfo_offset<C, LOGL, EPT, 3>(E) : fft2_vinfo_offset<C, LOGL, EPT>(E)) +
                       (size_t)V * sizeof(VecInfo);
   const bool simple = a.in_mode == IO_C && a.out_mode == IO_C && !a.pre_map && !a.pre_dc && !a.pre_dr &&
                       !a.pre_tw && !a.post_tw && !a.post_dc && !a.post_dr && !a.post_map && a.scale == (T)1 &&
                       !a.beta && a.in_fmul == 1 && a.in_fmod == 1 && a.out_fmul == 1 && a.out_fmod == 1;
-  if constexpr (has_rcap_variant<T, LOGL>() && ept_lmax<EPT>() > 3) {
+  if constexpr (MODE != 4 && has_rcap_variant<T, LOGL>() && ept_lmax<EPT>() > 3) {
     if (capped) {
       if constexpr (V > 1) {
         if (a.in_vcontig) return fft2_pick<T, LOGL, THREADS, EPT, true, 3>(a, simple, tiles, smem, st);
@@ -570,10 +625,15 @@ fm_status fft2_launch(FftArgs<T> a, cudaStream_t st) {
   if constexpr (sizeof(T) == 8 && LOGL >= 5 && LOGL <= 9) {
     if (a.small) return fft2_launch_cfg<T, LOGL, 2>(a, st);
   }
+  if constexpr (sizeof(T) == 4 && (LOGL == 9 || LOGL == 10)) {
+    // radix-32 tiles: by default for strided views of 2^10 (measured on GB300: the Kron
+    // circulant pass of 2^10 along a stride of 64, 350 -> 310 us), and where a.tile is 4
+    if (a.tile == 4 || (a.tile == 0 && LOGL == 10 && a.inner >= 16)) return fft2_launch_cfg<T, LOGL, 4>(a, st);
+  }
   if constexpr (LOGL >= 9 && LOGL + 4 <= maxloge) {
     // wide tiles for strided views by default (a.tile 0); a.tile 1 forces the default tile and
-    // 2 the wide one (the calibration's choice)
-    const bool wide = a.tile >= 2 ? a.inner > 1 : (a.tile == 1 ? false : a.inner >= 16);
+    // 2 or 3 the wide one (the calibration's choice)
+    const bool wide = (a.tile == 2 || a.tile == 3) ? a.inner > 1 : (a.tile == 1 ? false : a.inner >= 16);
     if (wide) return fft2_launch_cfg<T, LOGL, 1>(a, st);
   }
   return fft2_launch_cfg<T, LOGL, 0>(a, st);

@@ -123,6 +123,57 @@ template <typename C> __device__ __forceinline__ void dft16(C* a, int dir) {
   }
 }
 
+// x * W_32^m with W_32 = exp(dir * 2 pi i / 32), m = 0 .. 15.
+template <typename C, int M>
+__device__ __forceinline__ C w32(C x, int dir) {
+  typedef decltype(x.x) T;
+  if constexpr (M == 0) return x;
+  else if constexpr (M == 8) return cmul_i(x, dir);
+  else if constexpr (M == 4 || M == 12) {
+    const T h = (T)0.70710678118654752440084436210484903928;
+    return M == 4 ? cscale(cadd(x, cmul_i(x, dir)), h) : cscale(csub(cmul_i(x, dir), x), h);
+  } else {
+    // cos and sin of pi m / 16 from those of pi / 16, pi / 8 and 3 pi / 16 by symmetry
+    const T c1 = (T)0.98078528040323044912618223613424, s1 = (T)0.19509032201612826784828486847702;
+    const T c2 = (T)0.92387953251128675612818318939679, s2 = (T)0.38268343236508977172845998403040;
+    const T c3 = (T)0.83146961230254523707878837761791, s3 = (T)0.55557023301960222474283081394853;
+    constexpr int q = M < 8 ? M : 16 - M;  // cos(pi (16 - q) / 16) = -cos(pi q / 16), sin equal
+    T c, sn;
+    if constexpr (q == 1) { c = c1; sn = s1; }
+    else if constexpr (q == 2) { c = c2; sn = s2; }
+    else if constexpr (q == 3) { c = c3; sn = s3; }
+    else if constexpr (q == 5) { c = s3; sn = c3; }
+    else if constexpr (q == 6) { c = s2; sn = c2; }
+    else { c = s1; sn = c1; }  // q == 7
+    if constexpr (M > 8) c = -c;
+    const T sd = dir > 0 ? sn : -sn;
+    return cmake(x.x * c - x.y * sd, x.x * sd + x.y * c);
+  }
+}
+
+// In-register DFT of size 32 (natural order in and out): DFTs of length 16 over the even and
+// the odd elements, then y_k = E_k + W_32^k O_k and y_(k+16) = E_k - W_32^k O_k.
+template <typename C, int K = 0>
+__device__ __forceinline__ void dft32_combine(C* a, const C* e, const C* o, int dir) {
+  if constexpr (K < 16) {
+    const C t = w32<C, K>(o[K], dir);
+    a[K] = cadd(e[K], t);
+    a[K + 16] = csub(e[K], t);
+    dft32_combine<C, K + 1>(a, e, o, dir);
+  }
+}
+template <typename C> __device__ __forceinline__ void dft32(C* a, int dir) {
+  C e[16], o[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    e[i] = a[2 * i];
+    o[i] = a[2 * i + 1];
+  }
+  dft16(e, dir);
+  dft16(o, dir);
+  dft32_combine<C>(a, e, o, dir);
+}
+
 // Global-space loads and stores.  With the state space explicit (rather than a generic
 // address that might point into shared memory) the instruction scheduler may move a load
 // ahead of unrelated shared-memory stores, so a thread can have all the loads of a tile in

@@ -106,7 +106,7 @@ def test_split_rules(fm):
     with pytest.raises(fm.FmError):
         F.set_plan(1 << 16, 2, 4)         # radix cap 0 or 3 only
     with pytest.raises(fm.FmError):
-        F.set_plan(1 << 16, 1, 4)         # tile shapes 0 .. 3
+        F.set_plan(1 << 16, 1, 5)         # tile shapes 0 .. 4
 
 
 def _plan_cases(fm):
@@ -119,14 +119,17 @@ def _plan_cases(fm):
     Pref = O.Product(O.Partial(idx2, 4096), O.Diag(d2), O.Circulant(c2))
     F = fm.kron(fm.fourier(512), fm.fourier(32))
     Fref = O.Kron(O.Fourier(512), O.Fourier(32))
-    return [(K, Kref, 1024), (P, Pref, 4096), (F, Fref, 512)]
+    # a two-pass transform whose first pass is 2^10 along a stride of 256 (fused twiddles)
+    G = fm.fourier(1 << 18)
+    G.set_split(1 << 18, 1024)
+    return [(K, Kref, 1024), (P, Pref, 4096), (F, Fref, 512), (G, O.Fourier(1 << 18), 1 << 18)]
 
 
-@pytest.mark.parametrize("tile,rcap", [(0, 0), (1, 0), (2, 0), (3, 0), (0, 3), (1, 3), (2, 3), (3, 3)])
+@pytest.mark.parametrize("tile,rcap", [(0, 0), (1, 0), (2, 0), (3, 0), (4, 0), (0, 3), (1, 3), (2, 3), (3, 3), (4, 3)])
 def test_every_plan_choice_keeps_parity(fm, tile, rcap):
     # the compiled variants the calibration chooses among: tile shape of strided views and the
-    # radix schedule, on a Kron circulant of 2^10 along a stride, a 2^12 convolution tile and a
-    # 2^9 Fourier along a stride of 32
+    # radix schedule, on a Kron circulant of 2^10 along a stride, a 2^12 convolution tile, a
+    # 2^9 Fourier along a stride of 32 and the passes of a 2^18 Fourier transform
     for A, ref, L in _plan_cases(fm):
         A.set_plan(L, 1, tile)
         A.set_plan(L, 2, rcap)
