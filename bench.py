@@ -6,7 +6,8 @@ apply; the largest single-GPU workload of the metric).  ``value`` is whole-job G
 algorithmic bytes (read X + write Y per apply) with inputs resident in HBM; each buffer is
 four times the L2, so consecutive steps read cold data without a flush.  ``e2e`` is the
 same metric through the public API with pinned HOST buffers: H2D of X, forward, adjoint,
-D2H of the result, rotating over streams so that copies of one step overlap the others.
+D2H of the result, pipelined over three streams so that the copies in and out of
+neighbouring steps overlap each other and the compute.
 
 ``roofline`` is the dominant kernel of the step: its algorithmic bytes per launch over its
 device time, measured with the library's launch tracing (CUDA events around every launch)
@@ -429,29 +430,38 @@ def main():
     del Xk
 
     # ---- end to end through the public API with host buffers: every step copies its input
-    # from pinned host memory, runs forward + adjoint and copies the result back.  Steps
-    # rotate over two streams, each with its own operator (its own workspace) and buffers
-    # (three streams measured slower: 85 against 386 GB/s).
-    NE = 2
-    e2e_streams = [torch.cuda.Stream(dev) for _ in range(NE)]
-    Ke = [K] + [fm.kron(fm.hadamard(8), fm.circulant(ck), fm.fourier(64)) for _ in range(NE - 1)]
-    for k in Ke:
-        k.reserve(KRON_K, torch.complex64)
-    Xe = [X] + [torch.empty_like(X) for _ in range(NE - 1)]
-    Ye = [Y] + [torch.empty_like(X) for _ in range(NE - 1)]
-    Ze = [Z] + [torch.empty_like(X) for _ in range(NE - 1)]
-    out_h = [torch.empty_like(Xh).pin_memory() for _ in range(NE)]
+    # from pinned host memory, runs forward + adjoint and copies the result back.  Three
+    # streams form a pipeline (host-to-device copy of step i + 1, forward + adjoint of step i,
+    # device-to-host copy of step i - 1), with two input and two output buffers and events
+    # between the stages, so the host link carries both directions at once while the GPU
+    # computes; one operator on the compute stream.
+    NB = 2
+    s_in, s_cmp, s_out = (torch.cuda.Stream(dev) for _ in range(3))
+    Xe = [X, torch.empty_like(X)]
+    Ze = [Z, torch.empty_like(X)]
+    out_h = [torch.empty_like(Xh).pin_memory() for _ in range(NB)]
+    ev = {name: [torch.cuda.Event() for _ in range(NB)] for name in ("loaded", "read", "done", "drained")}
     e2e_steps = max(6, min(40, args.steps // 10))
 
     def e2e_step(i):
-        k = i % NE
-        with torch.cuda.stream(e2e_streams[k]):
+        k = i % NB
+        with torch.cuda.stream(s_in):
+            s_in.wait_event(ev["read"][k])          # the forward of step i - 2 has read Xe[k]
             Xe[k].copy_(Xh, non_blocking=True)
-            Ke[k].forward(Xe[k], out=Ye[k])
-            Ke[k].backward(Ye[k], out=Ze[k])
+            ev["loaded"][k].record(s_in)
+        with torch.cuda.stream(s_cmp):
+            s_cmp.wait_event(ev["loaded"][k])
+            s_cmp.wait_event(ev["drained"][k])      # step i - 2's result has left Ze[k]
+            K.forward(Xe[k], out=Y)
+            ev["read"][k].record(s_cmp)
+            K.backward(Y, out=Ze[k])
+            ev["done"][k].record(s_cmp)
+        with torch.cuda.stream(s_out):
+            s_out.wait_event(ev["done"][k])
             out_h[k].copy_(Ze[k], non_blocking=True)
+            ev["drained"][k].record(s_out)
 
-    for i in range(2 * NE):
+    for i in range(2 * NB):
         e2e_step(i)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -461,7 +471,7 @@ def main():
     t_e2e = time.perf_counter() - t0
     e2e_val = world * STEP_BYTES * e2e_steps / t_e2e / 1e9
     e2e_ok = all(bool(torch.equal(out_h[0], o)) for o in out_h[1:])
-    del Xe, Ye, Ze, Ke, out_h
+    del Xe, Ze, out_h
 
     # ---- cuFFT reference point: the same map as mode-wise torch.fft and a torch FWHT
     cufft = {}
@@ -503,7 +513,9 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "clocks": clk.summary(),
             "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": KRON_N * KRON_K * 8,
-                    "d2h_bytes_per_step": KRON_N * KRON_K * 8, "streams": NE, "steps": e2e_steps,
+                    "d2h_bytes_per_step": KRON_N * KRON_K * 8,
+                    "pipeline": "3 streams: copy in, forward + adjoint, copy out; 2 buffers each side",
+                    "steps": e2e_steps,
                     "results_agree": e2e_ok},
             "gpu_launches": int(launches),
             "roofline": roof,
