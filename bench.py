@@ -55,6 +55,7 @@ NCU_TRAFFIC = {
     "fwht_long_kernel": 90139392,
     # captured on one column of the Kron workload, scaled x4 to a 4-column launch
     "fft2_kernel<f32,L=2^10,strided,conv>": 4 * (134313472 + 91964160),
+    "fft2_kernel<f32,L=2^10,strided,conv,radix=32>": 4 * (134312448 + 92168960),
     "kron_hfc_kernel<8,6,cluster=2>": 4 * (134260736 + 85292544),
 }
 FISTA_INSTANCES = 4096
