@@ -77,24 +77,29 @@ struct Sched {
 // Shared-memory word of element t of tile vector v (VF: vectors fastest), one pad slot
 // every 16 words.
 //
-// SW: the layout of the radix-32 tiles of 2^10 (8 vectors), whose two exchanges write the
-// elements t = 32 j + k (k < 32) of butterfly j and read t = j + 32 k.  With t = 32 th + tl,
-// word = 264 th + 8 tl + v (VF) or 1056 v + 33 th + tl: both patterns step a register by a
-// constant, and in each half-warp (two values of th, or of tl, times 8 vectors; or 16 of them)
-// the 8-byte words fall in 16 distinct bank pairs, where the padded layout put four butterflies
-// on the same 8 pairs.
-template <bool VF, int LOGL, int LOGV, bool SW = false>
+// LAY 1: the layout of radix-32 tiles.  Strided tiles of 2^10 (8 vectors, VF) write the
+// elements t = 32 j + k (k < 32) of butterfly j in one exchange and read t = j + 32 k in the
+// other; with t = 32 th + tl, word = 264 th + 8 tl + v.  Tiles with contiguous vectors (not VF)
+// whose first pass has radix 32 take one pad slot every 32 words: word = v (L + L / 32) + t +
+// t / 32.  In both, every exchange pattern of the tile steps a register by a constant, and in
+// each half-warp the 8-byte words fall in 16 distinct bank pairs, where the layout with a pad
+// every 16 words puts two (contiguous) or four (strided) butterflies on the same pairs.
+template <bool VF, int LOGL, int LOGV, int LAY = 0>
 __device__ __forceinline__ int sp2(int t, int v) {
-  if constexpr (SW) {
-    static_assert(LOGL == 10 && LOGV == 3, "radix-32 layout: 8 vectors of 2^10");
-    return VF ? ((t >> 5) * 264 + (t & 31) * 8 + v) : (v * 1056 + (t >> 5) * 33 + (t & 31));
+  if constexpr (LAY == 1 && VF) {
+    static_assert(LOGL == 10 && LOGV == 3, "radix-32 layout of strided tiles: 8 vectors of 2^10");
+    return (t >> 5) * 264 + (t & 31) * 8 + v;
+  } else if constexpr (LAY == 1) {
+    return v * ((1 << LOGL) + (1 << (LOGL - 5))) + t + (t >> 5);
   } else {
     const int lin = VF ? ((t << LOGV) + v) : ((v << LOGL) + t);
     return lin + (lin >> 4);
   }
 }
-template <int EPT, int LOGL, int LOGV>
-__host__ __device__ constexpr bool sw_layout() { return EPT >= 32 && LOGL == 10 && LOGV == 3; }
+template <int EPT, int LOGL, int LOGV, bool VF>
+__host__ __device__ constexpr int layout_of() {
+  return EPT < 32 ? 0 : (VF ? ((LOGL == 10 && LOGV == 3) ? 1 : 0) : (Sched<LOGL, 5>::lr(0) == 5 ? 1 : 0));
+}
 
 // Butterfly q of this thread in a radix-2^LR pass: vector v, index j in [0, L/R).  THREADS is
 // the size of the thread group that owns the tile (the whole CTA, or one of its groups).
@@ -112,20 +117,29 @@ __device__ __forceinline__ void bfly2(int q, int& j, int& v) {
 
 // Elements t0 + k DT (k < R) of vector v: when the word step is a multiple of 16 the pad
 // slots between two of them are a constant too, so the addresses are one base plus
-// compile-time offsets (in the SW layout, DT = 1 from t0 = 32 j and DT = 32 from t0 < 32, the
-// steps are constants by construction).
+// compile-time offsets.  In the radix-32 layouts the steps are constants for DT = 1 (t0 = R j,
+// never across a pad) and, strided, DT = 32 or, contiguous, DT a multiple of 32.
 template <int DT, bool VF, int LOGV>
-__host__ __device__ constexpr int sw_step() {
-  return DT == 1 ? (VF ? (1 << LOGV) : 1) : (VF ? 264 : 33);
+__host__ __device__ constexpr int lay1_step() {
+  return VF ? (DT == 1 ? (1 << LOGV) : 264) : (DT == 1 ? 1 : DT + DT / 32);
 }
-template <bool VF, int LOGL, int LOGV, int DT, int R, bool SW, typename C>
+template <bool VF, int DT>
+__host__ __device__ constexpr bool lay1_const() {
+  return VF ? (DT == 1 || DT == 32) : (DT == 1 || DT % 32 == 0);
+}
+template <bool VF, int LOGL, int LOGV, int DT, int R, int LAY, typename C>
 __device__ __forceinline__ void s_gather(C* x, const C* s, int t0, int v) {
   constexpr int S = VF ? (DT << LOGV) : DT;
-  if constexpr (SW) {
-    static_assert(DT == 1 || DT == 32, "radix-32 layout: the two exchanges of a 2^10 tile");
-    const C* p = s + sp2<VF, LOGL, LOGV, true>(t0, v);
+  if constexpr (LAY == 1) {
+    static_assert(!VF || lay1_const<VF, DT>(), "radix-32 strided layout: the two exchanges of a 2^10 tile");
+    if constexpr (lay1_const<VF, DT>()) {
+      const C* p = s + sp2<VF, LOGL, LOGV, 1>(t0, v);
 #pragma unroll
-    for (int k = 0; k < R; ++k) x[k] = p[k * sw_step<DT, VF, LOGV>()];
+      for (int k = 0; k < R; ++k) x[k] = p[k * lay1_step<DT, VF, LOGV>()];
+    } else {
+#pragma unroll
+      for (int k = 0; k < R; ++k) x[k] = s[sp2<VF, LOGL, LOGV, 1>(t0 + k * DT, v)];
+    }
   } else if constexpr (S % 16 == 0) {
     const C* p = s + sp2<VF, LOGL, LOGV>(t0, v);
 #pragma unroll
@@ -135,14 +149,19 @@ __device__ __forceinline__ void s_gather(C* x, const C* s, int t0, int v) {
     for (int k = 0; k < R; ++k) x[k] = s[sp2<VF, LOGL, LOGV>(t0 + k * DT, v)];
   }
 }
-template <bool VF, int LOGL, int LOGV, int DT, int R, bool SW, typename C>
+template <bool VF, int LOGL, int LOGV, int DT, int R, int LAY, typename C>
 __device__ __forceinline__ void s_scatter(const C* x, C* s, int t0, int v) {
   constexpr int S = VF ? (DT << LOGV) : DT;
-  if constexpr (SW) {
-    static_assert(DT == 1 || DT == 32, "radix-32 layout: the two exchanges of a 2^10 tile");
-    C* p = s + sp2<VF, LOGL, LOGV, true>(t0, v);
+  if constexpr (LAY == 1) {
+    static_assert(!VF || lay1_const<VF, DT>(), "radix-32 strided layout: the two exchanges of a 2^10 tile");
+    if constexpr (lay1_const<VF, DT>()) {
+      C* p = s + sp2<VF, LOGL, LOGV, 1>(t0, v);
 #pragma unroll
-    for (int k = 0; k < R; ++k) p[k * sw_step<DT, VF, LOGV>()] = x[k];
+      for (int k = 0; k < R; ++k) p[k * lay1_step<DT, VF, LOGV>()] = x[k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < R; ++k) s[sp2<VF, LOGL, LOGV, 1>(t0 + k * DT, v)] = x[k];
+    }
   } else if constexpr (S % 16 == 0) {
     C* p = s + sp2<VF, LOGL, LOGV>(t0, v);
 #pragma unroll
@@ -160,7 +179,7 @@ __device__ __forceinline__ void p2_read(C (&r)[EPT], const C* s) {
   for (int q = 0; q < EPT / R; ++q) {
     int j, v;
     bfly2<VF, THREADS, LOGL, LOGV, LR>(q, j, v);
-    s_gather<VF, LOGL, LOGV, (1 << (LOGL - LR)), R, sw_layout<EPT, LOGL, LOGV>()>(&r[q * R], s, j, v);
+    s_gather<VF, LOGL, LOGV, (1 << (LOGL - LR)), R, layout_of<EPT, LOGL, LOGV, VF>()>(&r[q * R], s, j, v);
   }
 }
 
@@ -173,7 +192,7 @@ __device__ __forceinline__ void p2_write(const C (&r)[EPT], C* s) {
     int j, v;
     bfly2<VF, THREADS, LOGL, LOGV, LR>(q, j, v);
     const int base = ((j >> LOGNS) << (LOGNS + LR)) + (j & ((1 << LOGNS) - 1));
-    s_scatter<VF, LOGL, LOGV, (1 << LOGNS), R, sw_layout<EPT, LOGL, LOGV>()>(&r[q * R], s, base, v);
+    s_scatter<VF, LOGL, LOGV, (1 << LOGNS), R, layout_of<EPT, LOGL, LOGV, VF>()>(&r[q * R], s, base, v);
   }
 }
 

@@ -71,7 +71,7 @@ struct FistaArgs {
   int* counter;
 };
 
-constexpr int kFThreads = 1024, kFEpt = 16, kFE = kFThreads * kFEpt;  // 2^14 complex per tile
+constexpr int kFThreads = 512, kFEpt = 32, kFE = kFThreads * kFEpt;  // 2^14 complex per tile
 constexpr int kFMaxV = 64;                                                // n >= 256
 
 struct VState {
@@ -103,9 +103,16 @@ struct FGeo {
 __device__ __forceinline__ float2 ld_state(const float* p) { return __ldcg(reinterpret_cast<const float2*>(p)); }
 __device__ __forceinline__ void st_state(float* p, float2 v) { __stcg(reinterpret_cast<float2*>(p), v); }
 
+// word of element t of vector v in the tile (the layout the transform passes use)
+template <int LOGL>
+__device__ __forceinline__ int zword(int t, int v) {
+  constexpr bool VF = FGeo<LOGL>::VF;
+  constexpr int LOGV = FGeo<LOGL>::LOGV;
+  return sp2<VF, LOGL, LOGV, layout_of<kFEpt, LOGL, LOGV, VF>()>(t, v);
+}
 template <int LOGL>
 __device__ __forceinline__ float2* zaddr(float2* s, int t, int v) {
-  return &s[sp2<FGeo<LOGL>::VF, LOGL, FGeo<LOGL>::LOGV>(t, v)];
+  return &s[zword<LOGL>(t, v)];
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -278,7 +285,7 @@ __device__ void tile_spectral(float2* s, VState* vs, int adjoint, const float2* 
 
 template <int LOGL>
 __device__ __forceinline__ float unpack(const float2* s, int m, int v) {
-  const float2 z = s[sp2<FGeo<LOGL>::VF, LOGL, FGeo<LOGL>::LOGV>(m >> 1, v)];
+  const float2 z = s[zword<LOGL>(m >> 1, v)];
   return (m & 1) ? z.y : z.x;
 }
 
