@@ -37,6 +37,7 @@ struct FftArgs {
   int small = 0;            // 1: small tiles (passes of a small two-pass FP64 problem)
   int tile = 0;             // tile shape of strided views: 0 automatic, 1 default, 2 wide, 3 wide in 4 groups
   int rcap = 0;             // 3: radices of at most 8 (compiled for FP32 tiles of 2^9 .. 2^12)
+  int out_stage = 0;        // 1: outputs transposed through shared memory (set by the launcher)
   // input view
   const void* in = nullptr;
   int64_t in_ld = 0, in_ostride = 0, in_tstride = 1;

@@ -440,6 +440,43 @@ __device__ __forceinline__ void store_last(typename Cx<T>::t (&r)[EPT], const Ff
   }
 }
 
+// Outputs of the last pass through shared memory, for tiles whose vectors are contiguous on
+// the input side (consecutive threads on consecutive elements of a vector) but interleaved on
+// the output side (element t of vector v at t * out_fmul + v: the second pass of a long
+// transform).  The registers go to word t (V + 1) + v (both the write and the read below are
+// free of bank conflicts), then each thread stores elements of consecutive vectors, so a
+// warp's stores cover whole sectors instead of one 8-byte word in each of 32.  Plain complex
+// output with scale and accumulation only (the launcher checks).
+template <typename T, int THREADS, int EPT, int LOGL, int LOGV, int LR>
+__device__ __forceinline__ void store_staged(typename Cx<T>::t (&r)[EPT], typename Cx<T>::t* s, const FftArgs<T>& a,
+                                             const VecInfo* vinfo) {
+  typedef typename Cx<T>::t C;
+  constexpr int R = 1 << LR, M = 1 << (LOGL - LR), V = 1 << LOGV;
+  __syncthreads();  // every thread is done with the exchange buffer
+#pragma unroll
+  for (int q = 0; q < EPT / R; ++q) {
+    int j, v;
+    bfly2<false, THREADS, LOGL, LOGV, LR>(q, j, v);
+#pragma unroll
+    for (int k = 0; k < R; ++k) s[(j + k * M) * (V + 1) + v] = r[q * R + k];
+  }
+  __syncthreads();
+  const int fmul = (int)a.out_fmul, Lout = (int)a.Lout, ts = (int)a.out_tstride;
+#pragma unroll
+  for (int i = 0; i < EPT; ++i) {
+    const int e = (int)threadIdx.x + i * THREADS;
+    const int v = e & (V - 1), t = e >> LOGV;
+    const VecInfo& vi = vinfo[v];
+    const int n = t * fmul + vi.out_n2;
+    if (vi.out_off < 0 || n >= Lout) continue;
+    C y = s[t * (V + 1) + v];
+    if (a.scale != (T)1) y = cscale(y, a.scale);
+    C* p = reinterpret_cast<C*>(a.out) + vi.out_off + (int64_t)n * ts;
+    if (a.beta) y = cadd(y, gld(p));
+    gst(p, y);
+  }
+}
+
 // Resident CTAs per SM the register allocation is held to, for FP32 tiles: 4 x 256 threads
 // (32 warps per SM; at most a few registers spill), 3 x 256 for the convolution tiles of
 // 2^5, 2^6 and 2^9 (radix-8 passes with two butterflies per thread, whose spectrum product
@@ -535,6 +572,12 @@ __global__ void __launch_bounds__(THREADS, fft2_min_blocks<T, LOGL, THREADS, EPT
     p2_run<C, VF, TG, EPT, LOGL, LOGVG, 0, true, false, LM, THREADS>(r, sg, -a.dir0, a.tw);
     store_last<T, VF, SIMPLE, TG, EPT, LOGL, LOGVG, LR0>(r, a, vg);
   } else {
+    if constexpr (!VF && !SIMPLE && G == 1 && LOGV >= 4) {
+      if (a.out_stage) {
+        store_staged<T, THREADS, EPT, LOGL, LOGV, LRL>(r, s, a, vinfo);
+        return;
+      }
+    }
     store_last<T, VF, SIMPLE, TG, EPT, LOGL, LOGVG, LRL>(r, a, vg);
   }
 }
@@ -615,6 +658,11 @@ fm_status fft2_launch_cfg(FftArgs<T> a, cudaStream_t st) {
   const bool capped = MODE != 4 && has_rcap_variant<T, LOGL>() && a.rcap == 3 && ept_lmax<EPT>() > 3;
   const size_t smem = (capped ? fft2_vinfo_offset<C, LOGL, EPT, 3>(E) : fft2_vinfo_offset<C, LOGL, EPT>(E)) +
                       (size_t)V * sizeof(VecInfo);
+  // transposed outputs through shared memory (store_staged): contiguous input vectors (not
+  // VF), at least 16 of them, whose element t lands at t * out_fmul + (vector index)
+  a.out_stage = (V >= 16 && !(a.in_vcontig && V > 1) && !a.conv && a.out_mode == IO_C && !a.post_map && !a.post_dc &&
+                 !a.post_dr && !a.post_tw && a.inner == 1 && a.out_fdiv == 1 && a.out_fmul >= V && a.out_fmod >= V)
+                    ? 1 : 0;
   const bool simple = a.in_mode == IO_C && a.out_mode == IO_C && !a.pre_map && !a.pre_dc && !a.pre_dr &&
                       !a.pre_tw && !a.post_tw && !a.post_dc && !a.post_dr && !a.post_map && a.scale == (T)1 &&
                       !a.beta && a.in_fmul == 1 && a.in_fmod == 1 && a.out_fmul == 1 && a.out_fmod == 1;
