@@ -338,10 +338,12 @@ __device__ __forceinline__ void p2_run(C (&r)[EPT], C* s, int dir, const C* tw) 
 }
 
 // Two-pass twiddle W_N^(t n2) on the R elements t = j + k M of a butterfly (n2 = the
-// vector's column in the plan): one table read for j, one for the step M, then a recurrence.
-template <typename T, int R>
-__device__ __forceinline__ void tw_bfly(typename Cx<T>::t* x, const typename Cx<T>::t* tab, int64_t mask, int conj,
-                                        int j, int M, int64_t n2) {
+// vector's column in the plan): two table reads per butterfly (W^(j n2) and the step
+// W^(M n2)), then runs of H elements by recurrence, each run started from the previous one by
+// the step's H-th power (formed by squaring), so no product chain is longer than H + R / H.
+template <typename T, int R, int H>
+__device__ __forceinline__ void tw_butterfly(typename Cx<T>::t* x, const typename Cx<T>::t* tab, int64_t mask,
+                                             int conj, int j, int M, int64_t n2) {
   typedef typename Cx<T>::t C;
   C w = gld(tab + (((int64_t)j * n2) & mask));
   C ws = gld(tab + (((int64_t)M * n2) & mask));
@@ -349,10 +351,18 @@ __device__ __forceinline__ void tw_bfly(typename Cx<T>::t* x, const typename Cx<
     w = cconj(w);
     ws = cconj(ws);
   }
+  C wh = ws;
 #pragma unroll
-  for (int k = 0; k < R; ++k) {
-    x[k] = cmul(x[k], w);
-    if (k + 1 < R) w = cmul(w, ws);
+  for (int e = 1; e < H; e <<= 1) wh = cmul(wh, wh);
+#pragma unroll
+  for (int h = 0; h < R; h += H) {
+    C u = w;
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      x[h + k] = cmul(x[h + k], u);
+      if (k + 1 < H) u = cmul(u, ws);
+    }
+    if (h + H < R) w = cmul(w, wh);
   }
 }
 
@@ -397,9 +407,7 @@ __device__ __forceinline__ void load_first(typename Cx<T>::t (&r)[EPT], const Ff
     for (int q = 0; q < EPT / R; ++q) {
       int j, v;
       bfly2<VF, THREADS, LOGL, LOGV, LR>(q, j, v);
-#pragma unroll
-      for (int h = 0; h < R; h += H)
-        tw_bfly<T, H>(&r[q * R + h], a.pre_tw, a.tw_mask, a.pre_tw_conj, j + h * M, M, vinfo[v].tw_n2);
+      tw_butterfly<T, R, H>(&r[q * R], a.pre_tw, a.tw_mask, a.pre_tw_conj, j, M, vinfo[v].tw_n2);
     }
   }
 }
@@ -431,11 +439,9 @@ __device__ __forceinline__ void store_last(typename Cx<T>::t (&r)[EPT], const Ff
       }
     } else {
       constexpr int H = R > 8 ? 8 : R;
+      if (a.post_tw) tw_butterfly<T, R, H>(&r[q * R], a.post_tw, a.tw_mask, a.post_tw_conj, j, M, vi.tw_n2);
 #pragma unroll
-      for (int h = 0; h < R; h += H) {
-        if (a.post_tw) tw_bfly<T, H>(&r[q * R + h], a.post_tw, a.tw_mask, a.post_tw_conj, j + h * M, M, vi.tw_n2);
-        fft_store_bfly<T, H>(a, vi, j + h * M, M, &r[q * R + h]);
-      }
+      for (int h = 0; h < R; h += H) fft_store_bfly<T, H>(a, vi, j + h * M, M, &r[q * R + h]);
     }
   }
 }
