@@ -99,7 +99,9 @@ struct FGeo {
 };
 
 // x and y are rewritten by the kernel itself: read and write them through L2 (.cg), never
-// through the read-only path.
+// through the read-only path.  The spectra, row maps, measurements b and twiddle tables are
+// written before the launch and only read by it: those go through the read-only path (__ldg),
+// which also leaves the compiler free to issue them early.
 __device__ __forceinline__ float2 ld_state(const float* p) { return __ldcg(reinterpret_cast<const float2*>(p)); }
 __device__ __forceinline__ void st_state(float* p, float2 v) { __stcg(reinterpret_cast<float2*>(p), v); }
 
@@ -184,9 +186,9 @@ __device__ __forceinline__ void tile_fft_resid(float2* s, const VState* vs, cons
       float2 u = make_float2(0.f, 0.f);
       if (valid && kk < (Nc >> 1)) {
         const float2 z = r[q * R + k];
-        const int2 rr = *reinterpret_cast<const int2*>(inv + 2 * kk);
-        if (rr.x >= 0) u.x = z.x - bb[rr.x];
-        if (rr.y >= 0) u.y = z.y - bb[rr.y];
+        const int2 rr = __ldg(reinterpret_cast<const int2*>(inv + 2 * kk));
+        if (rr.x >= 0) u.x = z.x - __ldg(bb + rr.x);
+        if (rr.y >= 0) u.y = z.y - __ldg(bb + rr.y);
       }
       r[q * R + k] = u;
     }
@@ -248,6 +250,7 @@ template <int LOGL>
 __device__ void tile_spectral(float2* s, VState* vs, int adjoint, const float2* tw2) {
   constexpr int Nc = 1 << LOGL, half = Nc >> 1, V = FGeo<LOGL>::V;
   constexpr int tsh = 14 - LOGL;  // index scale into the W_{2^15} table for exp(-2 pi i k / (2 Nc))
+#pragma unroll 2
   for (int q = threadIdx.x; q < V * half; q += kFThreads) {
     const int v = q >> (LOGL - 1), k = q & (half - 1);
     if (!vs[v].valid) continue;
@@ -259,10 +262,10 @@ __device__ void tile_spectral(float2* s, VState* vs, int adjoint, const float2* 
     const float2 E = make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y));
     const float2 O = make_float2(0.5f * (Zk.y + Zm.y), -0.5f * (Zk.x - Zm.x));
     // W_{2Nc}^(Nc - k) = -conj(W_{2Nc}^k): one table read for the pair
-    const float2 wk = tw2[k << tsh], wkp = make_float2(-wk.x, wk.y);
+    const float2 wk = __ldg(tw2 + (k << tsh)), wkp = make_float2(-wk.x, wk.y);
     const float2 Wk = cadd(E, cmul(wk, O));
     const float2 Wkp = cadd(cconj(E), cmul(wkp, cconj(O)));
-    float2 sk = vs[v].spec[k], skp = vs[v].spec[kp];
+    float2 sk = __ldg(vs[v].spec + k), skp = __ldg(vs[v].spec + kp);
     if (adjoint) { sk = cconj(sk); skp = cconj(skp); }
     const float2 Vk = cscale(cmul(sk, Wk), 2.f), Vkp = cscale(cmul(skp, Wkp), 2.f);
     // Z'[k] = (V_k + conj V_kp)/2 + i exp(+2 pi i k / L) (V_k - conj V_kp)/2
@@ -277,7 +280,7 @@ __device__ void tile_spectral(float2* s, VState* vs, int adjoint, const float2* 
   for (int v = threadIdx.x; v < V; v += kFThreads) {
     if (!vs[v].valid) continue;
     float2* p = zaddr<LOGL>(s, half, v);
-    float2 c = cscale(vs[v].spec[half], 2.f);
+    float2 c = cscale(__ldg(vs[v].spec + half), 2.f);
     if (adjoint) c = cconj(c);
     *p = cmul(cconj(c), *p);
   }
@@ -326,10 +329,10 @@ __device__ void mask_rows(float2* s, VState* vs, double* part, bool sumsq) {
     double ss = 0.0;
     if (vs[v].valid && k < (Nc >> 1)) {
       const float2 z = MODE == MODE_B ? make_float2(0.f, 0.f) : *p;
-      const int2 r = *reinterpret_cast<const int2*>(vs[v].inv + 2 * k);
+      const int2 r = __ldg(reinterpret_cast<const int2*>(vs[v].inv + 2 * k));
       const float* bb = vs[v].b;
-      if (r.x >= 0) u.x = MODE == MODE_B ? bb[r.x] : (MODE == MODE_RESID ? z.x - bb[r.x] : z.x);
-      if (r.y >= 0) u.y = MODE == MODE_B ? bb[r.y] : (MODE == MODE_RESID ? z.y - bb[r.y] : z.y);
+      if (r.x >= 0) u.x = MODE == MODE_B ? __ldg(bb + r.x) : (MODE == MODE_RESID ? z.x - __ldg(bb + r.x) : z.x);
+      if (r.y >= 0) u.y = MODE == MODE_B ? __ldg(bb + r.y) : (MODE == MODE_RESID ? z.y - __ldg(bb + r.y) : z.y);
       ss = (double)u.x * (double)u.x + (double)u.y * (double)u.y;
     }
     *p = u;
