@@ -442,7 +442,7 @@ def main():
     Ze = [Z, torch.empty_like(X)]
     out_h = [torch.empty_like(Xh).pin_memory() for _ in range(NB)]
     ev = {name: [torch.cuda.Event() for _ in range(NB)] for name in ("loaded", "read", "done", "drained")}
-    e2e_steps = max(6, min(40, args.steps // 10))
+    e2e_steps = max(6, min(30, args.steps // 10))
 
     def e2e_step(i):
         k = i % NB
@@ -465,12 +465,16 @@ def main():
     for i in range(2 * NB):
         e2e_step(i)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for i in range(e2e_steps):
-        e2e_step(i)
-    torch.cuda.synchronize()
-    t_e2e = time.perf_counter() - t0
-    e2e_val = world * STEP_BYTES * e2e_steps / t_e2e / 1e9
+    # three timed runs of e2e_steps steps each; the value is their median (the host link's
+    # rate varies between runs of the same process: all three are reported)
+    e2e_runs = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        for i in range(e2e_steps):
+            e2e_step(i)
+        torch.cuda.synchronize()
+        e2e_runs.append(world * STEP_BYTES * e2e_steps / (time.perf_counter() - t0) / 1e9)
+    e2e_val = sorted(e2e_runs)[1]
     e2e_ok = all(bool(torch.equal(out_h[0], o)) for o in out_h[1:])
     del Xe, Ze, out_h
 
@@ -516,7 +520,7 @@ def main():
             "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": KRON_N * KRON_K * 8,
                     "d2h_bytes_per_step": KRON_N * KRON_K * 8,
                     "pipeline": "3 streams: copy in, forward + adjoint, copy out; 2 buffers each side",
-                    "steps": e2e_steps,
+                    "steps": e2e_steps, "runs_GB/s": e2e_runs, "value_is": "median of the three runs",
                     "results_agree": e2e_ok},
             "gpu_launches": int(launches),
             "roofline": roof,

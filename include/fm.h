@@ -262,7 +262,8 @@ fm_status fm_omp(fm_op A, const void* b, fm_dtype dt, int32_t K, void* x, int32_
  *           the Kron's length): 0 one CTA per [2^a][2^b] tile; 1 each tile on a cluster of two
  *           CTAs that combine the last Hadamard digit through distributed shared memory; 2 a
  *           cluster of four CTAs and the last two digits (tiles of at least 2^11 elements; a
- *           smaller tile takes the pair).
+ *           smaller tile takes the pair); 3 the pair, each CTA also prefetching into L2 its rows
+ *           of the tile half a residency wave later (the SM count / 2 tiles on).
  * fm_calibrate times A's forward + adjoint (one warm-up, mean of three) on ncols probe columns
  * of complex_of(dt) for every candidate of every setting of every transform in A, one setting
  * at a time (splits first, then per leaf the tile shape, then the radix schedule), and keeps

@@ -129,8 +129,8 @@ fm_status fm_set_plan(fm_op A, int64_t L, int32_t kind, int64_t value, void* str
   if (!A) { set_error("null operator"); return FM_ERR_INVALID_ARG; }
   if (kind == 0) return fm_set_split(A, L, value, stream);
   if ((kind == 1 && (value < 0 || value > 4)) || (kind == 2 && value != 0 && value != 3) ||
-      (kind == 3 && (value < 0 || value > 2)) || kind < 0 || kind > 3) {
-    set_error("plan setting %d = %lld: tile shape 0..4, radix cap 0 or 3, fused Kron pass 0..2", kind,
+      (kind == 3 && (value < 0 || value > 3)) || kind < 0 || kind > 3) {
+    set_error("plan setting %d = %lld: tile shape 0..4, radix cap 0 or 3, fused Kron pass 0..3", kind,
               (long long)value);
     return FM_ERR_INVALID_ARG;
   }
@@ -257,7 +257,7 @@ fm_status fm_calibrate(fm_op A, int64_t ncols, fm_dtype dt, void* stream, fm_tun
       const int kind = set.kind;
       int* field = kind == 2 ? &leaf->rcap : &leaf->tile;
       const std::vector<int> cand = kind == 1 ? std::vector<int>{0, 1, 2, 3, 4}
-                                  : kind == 2 ? std::vector<int>{0, 3} : std::vector<int>{0, 1, 2};
+                                  : kind == 2 ? std::vector<int>{0, 3} : std::vector<int>{0, 1, 2, 3};
       const int start = *field;
       int best = start;
       float best_ms = 0.f;

@@ -187,6 +187,18 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(hfc_threads<LA, LB,
       for (int k = 0; k < R; ++k) r[q * R + k] = gld(p + k * M);
     }
   }
+  // L2 prefetch of this CTA's rows of the tile a residency wave later, while this one computes
+  if (a.pf_tiles > 0 && tile + a.pf_tiles < a.ntiles) {
+    constexpr int LINES = ROWS * COLS * 8 / 128;  // 128-byte lines of this CTA's rows
+    const int64_t nt = tile + a.pf_tiles;
+    const int64_t ncol = nt / a.nmid, nmid = nt % a.nmid;
+    const float2* nin = a.in + ncol * a.in_ld + (nmid << LB) + (int64_t)rank * ROWS * a.sa;
+    for (int l = threadIdx.x; l < LINES; l += THREADS) {
+      constexpr int LPR = COLS * 8 / 128;  // lines per row
+      const float2* pl = nin + (int64_t)(l / LPR) * a.sa + (l % LPR) * 16;
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(pl)));
+    }
+  }
   p2_run<float2, false, THREADS, EPT, LB, LAL, 0, false, true>(r, s, a.dir, a.tw);
   __syncthreads();
   p2_write<float2, false, THREADS, EPT, LB, LAL, LRL, LB - LRL>(r, s);
@@ -226,7 +238,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(hfc_threads<LA, LB,
 }
 
 template <int LA, int LB, int CL>
-fm_status hfc_start(const KronHFArgs& a, cudaStream_t st) {
+fm_status hfc_start(KronHFArgs a, cudaStream_t st) {
   constexpr int E = 1 << (LA - ilog2c(CL) + LB);
   constexpr size_t smem = (size_t)(E + E / 16 + 1) * sizeof(float2);
   auto kern = kron_hfc_kernel<LA, LB, CL>;
@@ -240,6 +252,17 @@ fm_status hfc_start(const KronHFArgs& a, cudaStream_t st) {
   }
   if (a.ntiles == 0) return FM_OK;
   if (a.ntiles > 0x1fffffffLL) { set_error("kron_hf cluster: too many tiles"); return FM_ERR_UNSUPPORTED; }
+  if (a.pair == 3) {
+    // prefetch distance: half of the tiles resident on the GPU (two CTAs per SM, CL per tile);
+    // measured on GB300 for the 2^24 x 4 Kron workload: half a wave 265 us per launch, a whole
+    // wave 267, two waves 279, no prefetch 277
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      set_error("kron_hf cluster: SM count query failed");
+      return FM_ERR_CUDA;
+    }
+    a.pf_tiles = (int64_t)nsm / CL;
+  }
   static const std::string label =
       "kron_hfc_kernel<" + std::to_string(LA) + "," + std::to_string(LB) + ",cluster=" + std::to_string(CL) + ">";
   return pdl_go(label.c_str(), kern, dim3((unsigned)(CL * a.ntiles)), dim3(hfc_threads<LA, LB, CL>()), smem, st, a);
@@ -254,6 +277,7 @@ fm_status hf_pick(const KronHFArgs& a, cudaStream_t st) {
   if (a.pair == 2) {
     if constexpr (LA + LB >= 11) return hfc_start<LA, LB, 4>(a, st);
   }
+  if (a.pair == 3) return hfc_start<LA, LB, 2>(a, st);
   if (a.pair >= 1) return hfc_start<LA, LB, 2>(a, st);
   return hf_start<LA, LB>(a, st);
 }

@@ -18,7 +18,9 @@ struct KronHFArgs {
   float scale = 1.f;              // 1, or 1/sqrt(2^LB) for the orthonormal Fourier matrix
   int beta = 0;                   // 1: accumulate into out
   const float2* tw = nullptr;     // pass-twiddle tables (pass_tw_offset)
-  int pair = 0;                   // each tile on one CTA (0), a cluster of 2 (1) or of 4 CTAs (2)
+  int pair = 0;                   // each tile on one CTA (0), a cluster of 2 (1) or of 4 CTAs (2), or
+                                  // of 2 CTAs that prefetch a later tile's rows into L2 (3)
+  int64_t pf_tiles = 0;           // > 0: prefetch into L2 the rows of tile + pf_tiles (set by the launcher)
 };
 
 // Tiles [2^la][2^lb] with 2^10 <= 2^(la+lb) <= 2^14 and 4 <= la, lb <= 8.

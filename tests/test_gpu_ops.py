@@ -420,7 +420,7 @@ def test_kron_hadamard_strided_axis(fm, dt, la, lb):
     assert colerr(got, 2 * ref.apply(X.T.astype(np.complex128)).T) <= tol32(n)
 
 
-@pytest.mark.parametrize("pair", [0, 1, 2])
+@pytest.mark.parametrize("pair", [0, 1, 2, 3])
 @pytest.mark.parametrize("la,mid,lb,ortho", [(4, 4, 6, 0), (6, 3, 4, 1), (7, 2, 6, 0), (5, 1, 5, 0), (8, 1, 6, 1),
                                           (4, 1, 8, 0)])
 def test_kron_hadamard_fourier_fused(fm, la, mid, lb, ortho, pair):
@@ -463,7 +463,7 @@ def test_kron_workload_analogue(fm):
     assert colerr(got, (D @ X.T).T) <= tol32(4096)
 
 
-@pytest.mark.parametrize("pair", [0, 1, 2])
+@pytest.mark.parametrize("pair", [0, 1, 2, 3])
 def test_kron_workload_full_sampled(fm, pair):
     # Kron(H_256, C_1024, F_64) on 4 columns of length 2^24: sampled rows from the
     # definition and the adjoint identity at full size (both forms of the fused pass).
