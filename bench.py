@@ -56,7 +56,7 @@ NCU_TRAFFIC = {
     # captured on one column of the Kron workload, scaled x4 to a 4-column launch
     "fft2_kernel<f32,L=2^10,strided,conv>": 4 * (134313472 + 91964160),
     "fft2_kernel<f32,L=2^10,strided,conv,radix=32>": 4 * (134312448 + 92168960),
-    "kron_hfc_kernel<8,6,cluster=2>": 4 * (134260736 + 85292544),
+    "kron_hfc_kernel<8,6,cluster=2>": 4 * (134261760 + 85114112),
 }
 FISTA_INSTANCES = 4096
 FISTA_ITERS = 200
