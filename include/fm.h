@@ -263,7 +263,10 @@ fm_status fm_omp(fm_op A, const void* b, fm_dtype dt, int32_t K, void* x, int32_
  *           CTAs that combine the last Hadamard digit through distributed shared memory; 2 a
  *           cluster of four CTAs and the last two digits (tiles of at least 2^11 elements; a
  *           smaller tile takes the pair); 3 the pair, each CTA also prefetching into L2 its rows
- *           of the tile half a residency wave later (the SM count / 2 tiles on).
+ *           of the tile half a residency wave later (the SM count / 2 tiles on);
+ *   kind 5  (set only; the calibration does not time it) an FP32 or int8 Hadamard leaf of length
+ *           2^15 or 2^16 on plain column blocks (L = the leaf's n): 0 each CTA prefetches into
+ *           L2 its block of the column half a residency wave later (the default), 1 no prefetch.
  * fm_calibrate times A's forward + adjoint (one warm-up, mean of three) on ncols probe columns
  * of complex_of(dt) for every candidate of every setting of every transform in A, one setting
  * at a time (splits first, then per leaf the tile shape, then the radix schedule), and keeps
@@ -286,8 +289,8 @@ fm_status fm_calibrate(fm_op A, int64_t ncols, fm_dtype dt, void* stream, fm_tun
  * N1, L / N1 in [2^5, 2^13]; FM_OK if A has no transform of length L.  Same rules about
  * concurrent use as fm_calibrate. */
 fm_status fm_set_split(fm_op A, int64_t L, int64_t n1, void* stream);
-/* Set one plan setting (kind and value as in fm_tune_entry) of every FFT leaf (kinds 1, 2) or fused
- * Kron operator (kind 3) of length L in A,
+/* Set one plan setting (kind and value as in fm_tune_entry) of every FFT leaf (kinds 1, 2), fused
+ * Kron operator (kind 3) or long Hadamard leaf (kind 5) of length L in A,
  * e.g. to restore a cached calibration.  FM_ERR_INVALID_ARG for a value outside the kind's
  * range; FM_OK if A has no leaf of length L. */
 fm_status fm_set_plan(fm_op A, int64_t L, int32_t kind, int64_t value, void* stream);

@@ -61,6 +61,15 @@ void collect_kron(fm_op_s* A, std::vector<fm_op_s*>& out) {
   for (fm_op_s* k : A->kids) collect_kron(k, out);
 }
 
+// Hadamard leaves long enough for the long-column kernels (n >= 2^15, FP32 or int8 input).
+void collect_had(fm_op_s* A, std::vector<fm_op_s*>& out) {
+  if (!A) return;
+  if (A->kind == K_HADAMARD && A->log2n >= 15 && (A->had_mode == FM_HAD_FP32 || A->had_mode == FM_HAD_INT8)) {
+    if (std::find(out.begin(), out.end(), A) == out.end()) out.push_back(A);
+  }
+  for (fm_op_s* k : A->kids) collect_had(k, out);
+}
+
 void signature(const fm_op_s* A, std::string& out) {
   static const char* names[] = {"F", "C", "T", "H", "D", "P", "Prod", "Sum", "BlkDiag", "Kron", "Herm", "Blocks"};
   out += names[A->kind];
@@ -129,10 +138,18 @@ fm_status fm_set_plan(fm_op A, int64_t L, int32_t kind, int64_t value, void* str
   if (!A) { set_error("null operator"); return FM_ERR_INVALID_ARG; }
   if (kind == 0) return fm_set_split(A, L, value, stream);
   if ((kind == 1 && (value < 0 || value > 4)) || (kind == 2 && value != 0 && value != 3) ||
-      (kind == 3 && (value < 0 || value > 3)) || kind < 0 || kind > 3) {
-    set_error("plan setting %d = %lld: tile shape 0..4, radix cap 0 or 3, fused Kron pass 0..3", kind,
+      (kind == 3 && (value < 0 || value > 3)) || (kind == 5 && (value < 0 || value > 1)) || kind < 0 || kind == 4 ||
+      kind > 5) {
+    set_error("plan setting %d = %lld: tile shape 0..4, radix cap 0 or 3, fused Kron pass 0..3, Hadamard 0..1", kind,
               (long long)value);
     return FM_ERR_INVALID_ARG;
+  }
+  if (kind == 5) {
+    std::vector<fm_op_s*> hl;
+    collect_had(A, hl);
+    for (fm_op_s* h : hl)
+      if (h->rows == L) h->tile = (int)value;
+    return FM_OK;
   }
   if (kind == 3) {
     std::vector<fm_op_s*> kr;

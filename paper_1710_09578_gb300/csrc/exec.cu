@@ -577,6 +577,7 @@ static fm_status exec_hadamard(const fm_op_s* A, const View& in, const View& out
   a.out_ostride = out.ostride;
   a.out_tstride = out.inner;
   a.beta = beta;
+  a.prefetch = A->tile == 0 ? 1 : 0;
   if (ctx.dry) return FM_OK;
   if (A->had_mode == FM_HAD_BF16 || A->had_mode == FM_HAD_BF16X2)
     return fwht_mma_launch(a, A->had_mode == FM_HAD_BF16X2 ? 1 : 0, ctx.st);

@@ -10,6 +10,8 @@
 // the same time, so HBM sees each input byte about once.
 //
 // Element types: f32 -> f32, c64 -> c64 (as two real channels), int8 -> int32 (exact).
+#include <algorithm>
+
 #include "fm_device.cuh"
 #include "fm_internal.h"
 #include "fwht.h"
@@ -230,7 +232,7 @@ __device__ __forceinline__ int4 make_vec4(int a, int b, int c, int d) { return m
 
 template <typename Tin, typename W, int C>
 __global__ void __launch_bounds__(512, 2) fwht_long_kernel(const Tin* in, int64_t in_ld, W* out, int64_t out_ld,
-                                                           int beta) {
+                                                           int beta, int64_t ncols, int64_t pf_cols) {
   typedef typename Vec4<W>::t V4;
   constexpr int LP = 1 << 14;
   __shared__ __align__(32) W s[LP];
@@ -254,6 +256,15 @@ __global__ void __launch_bounds__(512, 2) fwht_long_kernel(const Tin* in, int64_
       ld8(x + (int64_t)sb * LP + 4096 * q, v);
 #pragma unroll
       for (int c = 0; c < 8; ++c) r[8 * q + c] = neg ? r[8 * q + c] - v[c] : r[8 * q + c] + v[c];
+    }
+  }
+  // L2 prefetch of block `part` of the column pf_cols further on (half a residency wave:
+  // the CTAs that will read it start about when this one's successors do), one line per thread
+  if (pf_cols > 0 && col + pf_cols < ncols) {
+    constexpr int LINES = LP * (int)sizeof(Tin) / 128;
+    if (t < LINES) {
+      const Tin* pl = in + (col + pf_cols) * in_ld + (int64_t)part * LP + t * (128 / (int)sizeof(Tin));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(pl)));
     }
   }
   wht_regs<W, 32>(r);
@@ -314,10 +325,22 @@ static fm_status fwht_long(const FwhtArgs& a, cudaStream_t st) {
   if (blocks == 0) return FM_OK;
   const char* nm = "fwht_long_kernel";
   const dim3 grid((unsigned)blocks), blk(512);
+  // prefetch distance: half of the columns resident on the GPU (two CTAs per SM, 2^logC per
+  // column); a.prefetch 0 turns it off
+  int64_t pf = 0;
+  if (a.prefetch) {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      set_error("fwht_long: SM count query failed");
+      return FM_ERR_CUDA;
+    }
+    pf = std::max<int64_t>(1, (int64_t)nsm >> logC);
+  }
+  const int64_t nc = a.ncols;
   switch (logC) {
-    case 0: return pdl_go(nm, fwht_long_kernel<Tin, W, 1>, grid, blk, 0, st, in, a.in_ld, out, a.out_ld, a.beta);
-    case 1: return pdl_go(nm, fwht_long_kernel<Tin, W, 2>, grid, blk, 0, st, in, a.in_ld, out, a.out_ld, a.beta);
-    case 2: return pdl_go(nm, fwht_long_kernel<Tin, W, 4>, grid, blk, 0, st, in, a.in_ld, out, a.out_ld, a.beta);
+    case 0: return pdl_go(nm, fwht_long_kernel<Tin, W, 1>, grid, blk, 0, st, in, a.in_ld, out, a.out_ld, a.beta, nc, pf);
+    case 1: return pdl_go(nm, fwht_long_kernel<Tin, W, 2>, grid, blk, 0, st, in, a.in_ld, out, a.out_ld, a.beta, nc, pf);
+    case 2: return pdl_go(nm, fwht_long_kernel<Tin, W, 4>, grid, blk, 0, st, in, a.in_ld, out, a.out_ld, a.beta, nc, pf);
     default: break;
   }
   set_error("fwht_long: unsupported length");

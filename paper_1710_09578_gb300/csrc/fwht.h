@@ -18,6 +18,7 @@ struct FwhtArgs {
   void* out = nullptr;
   int64_t out_ld = 0, out_ostride = 0, out_tstride = 1;
   int beta = 0;
+  int prefetch = 1;  // long contiguous columns: 1 prefetch a later column's blocks into L2, 0 not
 };
 
 fm_status fwht_launch(FwhtArgs a, fm_dtype in_dt, cudaStream_t st);

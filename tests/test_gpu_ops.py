@@ -178,23 +178,32 @@ def test_hadamard_bf16_tensor_cores(fm, log2n, mode, tol):
     assert colerr(got_b, want) <= tol
 
 
+@pytest.mark.parametrize("form", [0, 1])
 @pytest.mark.parametrize("log2n", [15, 16])
-def test_hadamard_long_columns_ld_and_sum(fm, log2n):
-    # long columns (two or four 2^14 blocks): padded leading dimensions on both sides, and
-    # a Sum whose second term accumulates into the first term's output
+def test_hadamard_long_columns_ld_and_sum(fm, log2n, form):
+    # long columns (two or four 2^14 blocks), with (form 0) and without (form 1) the L2
+    # prefetch of a later column: padded leading dimensions on both sides, and a Sum whose
+    # second term accumulates into the first term's output
     n = 1 << log2n
-    X = blk(3, n + 64, np.float32)
+
+    def had(mode=None):
+        H = fm.hadamard(log2n) if mode is None else fm.hadamard(log2n, mode)
+        H.set_plan(n, 5, form)
+        return H
+
+    X = blk(40, n + 64, np.float32)   # more columns than the prefetch distance on small GPUs
     want = O.Hadamard(n).apply(X[:, :n].T.astype(np.float64)).T
-    Yg = torch.zeros((3, n + 32), dtype=torch.float32, device=DEV)
-    fm.hadamard(log2n).forward(gpu(X)[:, :n], out=Yg[:, :n])
+    Yg = torch.zeros((40, n + 32), dtype=torch.float32, device=DEV)
+    had().forward(gpu(X)[:, :n], out=Yg[:, :n])
     assert colerr(Yg[:, :n].cpu().numpy(), want) <= tol32(n)
     assert torch.count_nonzero(Yg[:, n:]).item() == 0
     d = RNG.standard_normal(n).astype(np.float32)
-    S = fm.sum_(fm.hadamard(log2n), fm.hadamard(log2n), fm.diag(d))
+    S = fm.sum_(had(), had(), fm.diag(d))
     got = S.forward(gpu(X)[:, :n]).cpu().numpy()
     assert colerr(got, 2 * want + d * X[:, :n]) <= tol32(n)
     Xi = RNG.integers(-128, 128, size=(3, n + 64)).astype(np.int8)
-    gi = fm.hadamard(log2n, fm.FM_HAD_INT8).forward(gpu(Xi)[:, :n]).cpu().numpy()
+    Xi[0, :n] = -128                                  # extreme column: |y_0| = 128 n
+    gi = had(fm.FM_HAD_INT8).forward(gpu(Xi)[:, :n]).cpu().numpy()
     assert np.array_equal(gi.astype(np.int64), O.Hadamard(n).apply(Xi[:, :n].T.astype(np.int64)).T)
 
 
@@ -241,14 +250,17 @@ def test_hadamard_bf16_workload_full(fm):
         assert colerr(got, want) <= tol, mode
 
 
-def test_hadamard_workload_full(fm):
-    # the 2^16 x 256 block: FP32 within tolerance, int8 bit-exact
+@pytest.mark.parametrize("form", [0, 1])
+def test_hadamard_workload_full(fm, form):
+    # the 2^16 x 256 block with and without the L2 prefetch: FP32 within tolerance, int8 bit-exact
     xf, xi = I.hadamard_block()
     A = fm.hadamard(16)
+    A.set_plan(1 << 16, 5, form)
     got = A.forward(gpu(xf)).cpu().numpy()
     want = O.Hadamard(1 << 16).apply(xf.T.astype(np.float64)).T
     assert colerr(got, want) <= tol32(1 << 16)
     Ai = fm.hadamard(16, fm.FM_HAD_INT8)
+    Ai.set_plan(1 << 16, 5, form)
     gi = Ai.forward(gpu(xi)).cpu().numpy()
     assert np.array_equal(gi.astype(np.int64), O.Hadamard(1 << 16).apply(xi.T).T)
 
