@@ -266,7 +266,7 @@ fm_status fm_omp(fm_op A, const void* b, fm_dtype dt, int32_t K, void* x, int32_
  *           of the tile half a residency wave later (the SM count / 2 tiles on);
  *   kind 5  (set only; the calibration does not time it) an FP32 or int8 Hadamard leaf of length
  *           2^15 or 2^16 on plain column blocks (L = the leaf's n): 0 each CTA prefetches into
- *           L2 its block of the column half a residency wave later (the default), 1 no prefetch.
+ *           L2 its block of the column one residency wave later (the default), 1 no prefetch.
  * fm_calibrate times A's forward + adjoint (one warm-up, mean of three) on ncols probe columns
  * of complex_of(dt) for every candidate of every setting of every transform in A, one setting
  * at a time (splits first, then per leaf the tile shape, then the radix schedule), and keeps
