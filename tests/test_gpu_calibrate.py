@@ -136,3 +136,43 @@ def test_every_plan_choice_keeps_parity(fm, tile, rcap):
         X = I.column_block(RNG, 3, A.cols, np.complex64)
         Y = I.column_block(RNG, 3, A.rows, np.complex64)
         _check(A, ref, X, Y, 1e-5 * 18)
+
+
+@pytest.mark.parametrize("inner", [2, 4, 16, 32])
+@pytest.mark.parametrize("tile", [0, 4])
+def test_radix32_tiles_ragged(fm, inner, tile):
+    # the radix-32 tile of 2^10 along a stride (vectors side by side, 8 per tile) with vector
+    # counts that leave a partial last tile or let a tile span two outer indices, and the same
+    # tile on contiguous vectors (a plain circulant on 5 columns) and at 2^9
+    rng = np.random.default_rng(41)
+    c = I.cn(rng, (1024,))
+    K = fm.kron(fm.hadamard(1), fm.circulant(c), fm.fourier(inner))
+    K.set_plan(1024, 1, tile)
+    Kref = O.Kron(O.Hadamard(2), O.Circulant(c), O.Fourier(inner))
+    X = I.column_block(RNG, 3, K.cols, np.complex64)
+    Y = I.column_block(RNG, 3, K.rows, np.complex64)
+    _check(K, Kref, X, Y, 1e-5 * 18)
+    for n in (512, 1024):
+        C = fm.circulant(c[:n])
+        C.set_plan(n, 1, tile)
+        X = I.column_block(RNG, 5, n, np.complex64)
+        _check(C, O.Circulant(c[:n]), X, X, 1e-5 * 10)
+
+
+@pytest.mark.parametrize("n1", [32, 64, 256, 1024, 2048])
+def test_two_pass_staged_outputs(fm, n1):
+    # a 2^16 Fourier transform under every split with its second pass's interleaved outputs
+    # (staged through shared memory where the tile holds 16 or more rows), forward and
+    # adjoint, and a Sum whose second term accumulates into the first's output
+    n = 1 << 16
+    F = fm.fourier(n)
+    F.set_split(n, n1)
+    X = I.column_block(RNG, 3, n, np.complex64)
+    _check(F, O.Fourier(n), X, X, 1e-5 * 16)
+    G = fm.fourier(n)
+    G.set_split(n, n1)
+    S = fm.sum_(F, G)
+    got = S.forward(gpu(X)).cpu().numpy()
+    want = 2 * O.Fourier(n).apply(X.T.astype(np.complex128)).T
+    err = np.linalg.norm(got - want, axis=1) / np.linalg.norm(want, axis=1)
+    assert err.max() <= 1e-5 * 16
