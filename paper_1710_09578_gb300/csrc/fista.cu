@@ -93,8 +93,9 @@ template <int LOGL>
 struct FGeo {
   static constexpr int LOGV = 14 - LOGL, V = 1 << LOGV, NC = 1 << LOGL;
   // elements of a vector contiguous in shared memory: the element-wise steps (spectral
-  // step, row mask, update) walk consecutive elements of one vector, and every transform
-  // length here (n >= 256) gives a warp 32 consecutive butterflies of one vector
+  // step, row mask, update) walk consecutive elements of one vector, and in the transform
+  // passes a warp's lanes take consecutive butterflies of one vector (of two for the radix-16
+  // passes of n = 256, which have 16 butterflies per vector)
   static constexpr bool VF = false;
 };
 
