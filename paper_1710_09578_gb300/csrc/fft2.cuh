@@ -1,7 +1,8 @@
 // Tile FFT kernel with the transform length fixed at compile time.
 //
-// V vectors of length L per CTA, radix-16 (then 8/4/2) Stockham passes with the elements of each
-// butterfly in registers (the DFT of Eq. (1) by the butterfly factorisation of Sec. 1) and
+// V vectors of length L per CTA, radix-16 (then 8/4/2) Stockham passes, or radix-32 passes where
+// a thread holds 32 elements, with the elements of each butterfly in registers (the DFT of
+// Eq. (1) by the butterfly factorisation of Sec. 1) and
 // the spectrum product of a circulant (Eq. (5)) in registers between the last forward and
 // the first inverse pass.  With L a template parameter the radix schedule, the
 // thread-to-butterfly mapping and every in-tile index are compile-time constants, so the
@@ -12,8 +13,10 @@
 // only carries the exchanges between passes.  The thread-to-butterfly mapping follows the
 // layout in HBM: VF (vectors contiguous, a strided axis) gives consecutive threads
 // consecutive vectors, otherwise consecutive threads take consecutive elements of a
-// vector, so each warp access is a few full 32-byte sectors either way.  A thread issues
-// all of its loads before the first shared-memory store.  Loads and stores go through the
+// vector, so each warp access is a few full 32-byte sectors either way (a second pass whose
+// contiguous rows land interleaved in the output transposes them through shared memory
+// first: store_staged).  A thread issues all of its loads before the first shared-memory
+// store.  Loads and stores go through the
 // per-vector table and the fused pre/post operations of FftArgs (Diag, row selection,
 // zero-padding and truncation, two-pass twiddles, scale, accumulation).
 #pragma once
