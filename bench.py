@@ -52,7 +52,7 @@ HAD_APPLY_BYTES = 2 * HAD_N * HAD_K * 4
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it is now
 # (dram__bytes_read.sum + dram__bytes_write.sum); None where no current capture exists.
 NCU_TRAFFIC = {
-    "fwht_long_kernel": 67142144 + 22341376,
+    "fwht_long_kernel": 67134464 + 22094080,
     # captured on one column of the Kron workload, scaled x4 to a 4-column launch
     "fft2_kernel<f32,L=2^10,strided,conv>": 4 * (134313472 + 91964160),
     "fft2_kernel<f32,L=2^10,strided,conv,radix=32>": 4 * (134312448 + 92168960),
